@@ -1,0 +1,358 @@
+"""Benchmark of the batched SPIR-V hot path on B300.
+
+One step = the whole hot path over one batch of synthetic modules:
+decode + validate + encode in one persistent launch (spv_process_batch),
+then disassembly with inline names and header lines (spv_disassemble_batch).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload batch|large|single]
+                    [--impl gpu|reference]
+
+The default workload is the batch of 10,000 synthetic kernel modules
+(instruction counts lognormal, median 1,500, 1-8 kernels each; ~122M words).
+Prints one JSON line (rank 0). Under torchrun each rank processes its own
+batch of the same shape (different seeds): weak scaling, no data-path
+collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPIR-V GB/s decode+validate+disasm, batched vs per-module; serve p50/p99 latency"
+L2_BYTES = 126 * 2**20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="batch", choices=["batch", "large", "single"])
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-per-module", action="store_true", help="skip the per-module comparison leg")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--modules", type=int, default=10_000, help="modules in the batch workload")
+    return ap.parse_args()
+
+
+def workload(name, rank, n_mod=10_000):
+    from paper_2305_09493_b300 import synth
+    if name == "batch":
+        w, off = synth.module_batch(n_mod, seed0=rank * n_mod)
+        cfg = {"workload": f"batch of {n_mod:,} synthetic kernel modules", "modules": n_mod,
+               "instr_per_module": "lognormal median 1500 sigma 1.0 clip [200, 50000]", "kernels_per_module": "1-8"}
+    elif name == "large":
+        w, off, _, _ = synth.large_module(seed=rank)
+        cfg = {"workload": "one module of 4M instructions, 500 functions, 10% OpString/OpName", "modules": 1}
+    else:
+        w, off, _, _ = synth.single_module(seed=rank)
+        cfg = {"workload": "one ~10k-word kernel module (2,000-instruction function, 40 blocks)", "modules": 1}
+    cfg["words"] = int(len(w))
+    return w, off, cfg
+
+
+def dist_setup(n):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    return rank, world
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2305_09493_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].strip() == "Active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# algorithmic bytes per launch of each kernel (W words, N rows, L text bytes, M modules)
+def algorithmic_bytes(kernel, W, N, L, M):
+    return {
+        "k_tile": 4 * W + 4 * W + 24 * N,                # words in; encoded words + 24-byte rows out
+        "k_dis_write_rows": 4 * W + 24 * N + L,          # words + op/wc/off/mod + row positions in; text out
+        "k_dis_len": 4 * W + 16 * N + 8 * N,             # words + op/wc/off/mod in; row positions out
+        "k_dis_ids": 20 * N,                             # op/wc/off/mod/rid columns
+        "k_dis_clear": 0, "k_tiles": 0, "k_prepass": 40 * M, "k_finalize": 64 * M,
+    }.get(kernel, 0)
+
+
+def cpu_baseline(words, mod_off, budget_s=12.0):
+    """The oracle (plain sequential C, one thread) on a bounded sample: the
+    first modules of the batch, as many as fit the time budget."""
+    import oracle
+    m_total = len(mod_off) - 1
+    k = max(1, min(m_total, 200))
+    t0 = time.perf_counter()
+    while True:
+        sub = words[mod_off[0]:mod_off[k]]
+        off = mod_off[:k + 1] - mod_off[0]
+        t = time.perf_counter()
+        d = oracle.decode(sub, off)
+        oracle.validate(sub, off)
+        oracle.encode(sub, off, d, True)
+        oracle.disassemble(sub, off, True, True)
+        dt = time.perf_counter() - t
+        if dt > budget_s / 3 or k == m_total or time.perf_counter() - t0 > budget_s:
+            break
+        k = min(m_total, int(k * max(2.0, budget_s / 2 / max(dt, 1e-3))))
+    gbs = 4 * len(sub) / dt / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {k} of {m_total} modules ({len(sub)} words): decode+validate+encode+disassemble, "
+                      f"{dt:.2f} s on one host core"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w, off, cfg = workload(args.workload, 0, args.modules)
+    for _ in range(args.warmup):
+        cpu_baseline(w, off, budget_s=2.0)
+    vals = []
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(w, off, budget_s=8.0)
+        vals.append(last["value"])
+    v = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": last["sample"], "value": v, "unit": "GB/s"},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, world = dist_setup(args.gpus)
+    from paper_2305_09493_b300 import build, spvgpu
+    build.build()
+    spvgpu.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w_np, off_np, cfg = workload(args.workload, rank, args.modules)
+    W, M = len(w_np), len(off_np) - 1
+    words = torch.from_numpy(w_np.view(np.int32)).to(dev)
+    mod_off = torch.from_numpy(off_np).to(dev)
+    stream = torch.cuda.current_stream()
+
+    # resident outputs and workspaces, reused by every step
+    table = spvgpu.Table(M, W, dev)
+    ws = spvgpu.Workspace(M, W, dev)
+    out = torch.empty_like(words)
+    dws = spvgpu.DisWorkspace(M, W, W, dev)
+    r = spvgpu.process(words, mod_off, encode=True, table=table, workspace=ws, out=out)
+    text, text_off, dst = spvgpu.disassemble(words, mod_off, table, workspace=dws)
+    torch.cuda.synchronize()
+    N = int(table.mod_first_row[-1].item())
+    Ltext = int(text_off[-1].item())
+    status_ok = bool((r["status"] == 0).all().item()) and bool((dst == 0).all().item())
+    text_buf = torch.empty(Ltext + 1, dtype=torch.uint8, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev) if 4 * W < 2 * L2_BYTES else None
+
+    def step():
+        spvgpu.process(words, mod_off, encode=True, table=table, workspace=ws, out=out)
+        spvgpu.disassemble(words, mod_off, table, workspace=dws, text=text_buf, sync=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    clocks = Clocks(torch.cuda.current_device())
+    spvgpu.profile_enable(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        if flush is not None:
+            flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    prof = spvgpu.profile_read()
+    spvgpu.profile_enable(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_ms = float(np.sum(step_ms))
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    value = world * 4 * W / (ms_per_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel
+    launches = sum(v[0] for v in prof.values())
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    kname, (kl, kms) = top
+    per_launch_ms = kms / kl
+    alg = algorithmic_bytes(kname, W, N, Ltext, M)
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (per_launch_ms * 1e-3) / 1e9
+    traffic = None
+    tj = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tj):
+        t = json.load(open(tj))
+        if t.get("kernel") == kname and t.get("source_sha") == source_hash() and t.get("workload") == args.workload:
+            traffic = t.get("bytes_per_launch")
+    kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in
+               sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # end to end: pinned host buffers, copies inside the timed region
+    h_words = torch.from_numpy(w_np.view(np.int32)).pin_memory()
+    h_off = torch.from_numpy(off_np).pin_memory()
+    h_status = torch.empty(M, dtype=torch.int32).pin_memory()
+    h_err = torch.empty(M, dtype=torch.int64).pin_memory()
+    h_toff = torch.empty(M + 1, dtype=torch.int64).pin_memory()
+    h_text = torch.empty(Ltext + 1, dtype=torch.uint8).pin_memory()
+    e_words = torch.empty_like(words)
+    e_off = torch.empty_like(mod_off)
+
+    def e2e_step():
+        e_words.copy_(h_words, non_blocking=True)
+        e_off.copy_(h_off, non_blocking=True)
+        rr = spvgpu.process(e_words, e_off, encode=True, table=table, workspace=ws, out=out)
+        _, toff, _ = spvgpu.disassemble(e_words, e_off, table, workspace=dws, text=text_buf, sync=False)
+        h_status.copy_(rr["status"], non_blocking=True)
+        h_err.copy_(rr["err_row"], non_blocking=True)
+        h_toff.copy_(toff, non_blocking=True)
+        h_text.copy_(text_buf, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ksteps = max(1, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(ksteps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / ksteps
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e = {"value": world * 4 * W / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": 4 * W + 8 * (M + 1),
+           "d2h_bytes_per_step": 4 * M + 8 * M + 8 * (M + 1) + (Ltext + 1),
+           "ms_per_step": e2e_ms}
+
+    # batched vs per-module launches (decode+validate+encode, same exact output)
+    cmp = None
+    if not args.no_per_module and world == 1:
+        def process_only(cfg_):
+            spvgpu.process(words, mod_off, encode=True, table=table, workspace=ws, out=out, cfg=cfg_)
+        res = {}
+        for label, cfg_ in (("batched", None), ("per_module", spvgpu.make_config(per_module=1))):
+            process_only(cfg_)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3 if label == "batched" else 1
+            if flush is not None:
+                flush.zero_()
+            a.record(stream)
+            for _ in range(reps):
+                process_only(cfg_)
+            b.record(stream)
+            torch.cuda.synchronize()
+            res[label] = 4 * W / (a.elapsed_time(b) / reps * 1e-3) / 1e9
+        cmp = {"scope": "decode+validate+encode", "batched_gbs": res["batched"], "per_module_gbs": res["per_module"],
+               "speedup": res["batched"] / res["per_module"]}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w_np, off_np)
+    cfg.update({"rows": N, "text_bytes": Ltext, "l2": "inputs larger than L2" if flush is None else
+                "L2 flushed (252 MiB write) between timed steps", "parallelism": f"{world} GPU(s), one batch each",
+                "all_status_ok": status_ok})
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": cfg,
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg, "ms_per_launch": per_launch_ms},
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "batched_vs_per_module": cmp,
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * spv.h -- C ABI of the batched SPIR-V library for NVIDIA B300 (sm_103a).
+ *
+ * The library decodes, validates, re-encodes and disassembles many SPIR-V
+ * binary modules at once on one GPU. It implements the data-parallel core of
+ * the toolkit described in arXiv 2305.09493 ("Experiences in Building a
+ * Composable and Functional API for Runtime SPIR-V Code Generation"):
+ *   decode       the binary layout of section 3.4.6 ("Compliance": modules are
+ *                32-bit words holding opcodes and operands) and Listing 4
+ *                (header: version, generator, bound, schema);
+ *   validate     the rules of section 3.4.5 plus the SSA rule of section 3.4.2;
+ *   encode       section 3.2.1 (instructions write themselves as words) with
+ *                the write-time bound recomputation of section 3.4.1;
+ *   disassemble  section 3.4.4 with the "inline names" and "header" options
+ *                of Listing 10, one line per instruction as in Listing 8.
+ *
+ * Conventions for every call below.
+ *   - All array arguments are DEVICE pointers unless marked "host". They are
+ *     owned by the caller; the library never frees or keeps them.
+ *   - Calls are asynchronous on the given CUDA stream and never synchronise
+ *     unless stated. A call returns a negative SPV_E_* code when an argument
+ *     is invalid or a CUDA call fails (nothing is launched in the first case);
+ *     per-module results go to status[] and never make a call fail.
+ *   - "workspace" is caller-owned device scratch of at least the size the
+ *     matching *_workspace_bytes function returns. It is fully rewritten by
+ *     each call; two calls that overlap on the GPU must not share one.
+ *   - Module m is words[mod_off[m] .. mod_off[m+1]) (little-endian 32-bit
+ *     words, never byte-swapped); mod_off is non-decreasing, mod_off[0] = 0,
+ *     mod_off[n_modules] = n_words, every module is shorter than 2^31 words.
+ */
+#ifndef SPV_H
+#define SPV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *spv_stream_t;   /* a cudaStream_t; NULL = legacy default stream */
+
+/* Per-module status codes (status[m]). When several errors apply the one at
+ * the lowest instruction index wins; within one instruction the order is
+ * UNKNOWN_OPCODE, BAD_OPERANDS, ID_OUT_OF_BOUND, DUP_RESULT_ID,
+ * MISSING_CAPABILITY; a framing error (TRUNCATED, ZERO_WORDCOUNT) counts as
+ * the instruction after the last decoded one; module-level rules
+ * (NO_CAPABILITY .. NO_FUNCTION) apply only when no instruction-level error
+ * exists. */
+enum spv_status {
+    SPV_OK = 0,
+    SPV_BAD_MAGIC = 1,          /* word 0 is not 0x07230203 */
+    SPV_BAD_HEADER = 2,         /* version word not 0x00MMmm00 with major 1, minor <= 6; or schema != 0 */
+    SPV_TRUNCATED = 3,          /* fewer than 5 words, or an instruction runs past the module's end */
+    SPV_ZERO_WORDCOUNT = 4,     /* an instruction's word count is 0 */
+    SPV_UNKNOWN_OPCODE = 5,     /* opcode outside the library's compute-subset table */
+    SPV_BAD_OPERANDS = 6,       /* operand words do not match the opcode's operand list */
+    SPV_ID_OUT_OF_BOUND = 7,    /* an id operand, result type or result id is 0 or >= bound */
+    SPV_DUP_RESULT_ID = 8,      /* a result id defined by an earlier instruction */
+    SPV_NO_CAPABILITY = 9,      /* no OpCapability (section 3.4.5) */
+    SPV_NO_MEMORY_MODEL = 10,   /* no OpMemoryModel (section 3.4.5) */
+    SPV_MULTI_MEMORY_MODEL = 11,/* more than one OpMemoryModel */
+    SPV_NO_ENTRY_POINT = 12,    /* no OpEntryPoint (section 3.4.5) */
+    SPV_NO_FUNCTION = 13,       /* no OpFunction (section 3.4.5) */
+    SPV_MISSING_CAPABILITY = 14,/* an instruction needs a capability the module does not declare */
+    SPV_TIMEOUT = 15,           /* a bounded wait inside a kernel gave up; results of the module are void */
+    SPV_CAPACITY = 16           /* output rows or workspace arena too small for this module */
+};
+
+/* Call-level return codes. */
+#define SPV_SUCCESS 0
+#define SPV_E_ARG (-1)          /* invalid argument; nothing was launched */
+#define SPV_E_WORKSPACE (-2)    /* workspace smaller than required; nothing was launched */
+#define SPV_E_CUDA (-3)         /* a CUDA launch or runtime call failed */
+#define SPV_E_UNSUPPORTED (-4)  /* requested configuration not available */
+
+/* A batch of modules (device pointers). */
+typedef struct spv_batch {
+    const uint32_t *words;      /* [n_words] */
+    const int64_t *mod_off;     /* [n_modules + 1] */
+    int32_t n_modules;
+    int64_t n_words;
+} spv_batch;
+
+/* The structure-of-arrays instruction table (one row per decoded
+ * instruction, rows of module m contiguous and in module order). All columns
+ * are device arrays of capacity_rows entries written by decode; the per-module
+ * arrays have n_modules (+1) entries. A decode call writes mod_first_row[m]
+ * (first row of module m) for every m and mod_first_row[n_modules] = total
+ * rows; rows beyond capacity_rows are not written and their modules get
+ * SPV_CAPACITY. capacity_rows >= n_words always suffices. */
+typedef struct spv_table {
+    uint16_t *op;               /* opcode */
+    uint16_t *wc;               /* word count */
+    uint64_t *off;              /* absolute word index of the instruction in batch.words */
+    uint32_t *rtype;            /* result type id, 0 if the opcode has none */
+    uint32_t *rid;              /* result id, 0 if the opcode has none */
+    uint32_t *mod;              /* module index */
+    int64_t *mod_first_row;     /* [n_modules + 1] */
+    uint32_t *mod_n_instr;      /* [n_modules] */
+    int64_t capacity_rows;
+} spv_table;
+
+/* Tuning of the batched kernels; zero fields take defaults. */
+typedef struct spv_config {
+    int32_t tile_words;         /* words per tile: 1024, 2048, 4096 or 8192 (default 4096) */
+    int32_t threads;            /* threads per CTA: 128 or 256 (default 256); tile_words/threads must be 8 or 16 */
+    int32_t ctas_per_sm;        /* resident CTAs per SM for the persistent grid (default: occupancy maximum) */
+    int32_t per_module;         /* 1: one launch sequence per module instead of one persistent launch
+                                   (comparison path; copies mod_off to the host and synchronises) */
+    int64_t max_spins;          /* bound on every wait inside a kernel (0: default 1 << 20 polls); a
+                                   wait that runs out ends with SPV_TIMEOUT for every module of the call */
+    int64_t test_stall_tile;    /* test hook, 0 = off: with n > 0, tile n-1 never publishes its look-back
+                                   states, so the waits of the tiles after it run out */
+} spv_config;
+
+/* Workspace bytes needed by spv_process_batch / spv_decode_batch /
+ * spv_validate_batch for a batch of this shape. arena_words is the capacity,
+ * in 32-bit words, of the arena holding each module's set of result ids: a
+ * bitmap of ceil(bound / 32) words when bound <= 32 * (len + 64), else a
+ * hash set of 2 * len + 64 words (len = the module's words). 0 selects the
+ * default 2 * n_words + 64 * n_modules + 64, which always fits every module;
+ * with a smaller arena the modules that do not fit get SPV_CAPACITY. */
+size_t spv_workspace_bytes(int32_t n_modules, int64_t n_words, int64_t arena_words, const spv_config *cfg);
+
+/*
+ * spv_process_batch -- decode (+ validate) (+ encode) in one persistent launch.
+ *
+ * Decode (Listing 4 header; section 3.4.6 word layout): per module check the
+ * header, then walk instructions from word 5 by the word count in the high
+ * half of each instruction's first word, stopping at the first word count of
+ * 0 or at an instruction running past the module's end; fill the table.
+ * validate != 0 adds the rules of section 3.4.5 and the id rules of section
+ * 3.4.2 (status codes above). out_words != NULL re-encodes every module into
+ * out_words[n_words] (same offsets): each instruction's first word, result
+ * type and result id are written from the decoded columns, every other word
+ * is copied, and with recompute_bound the header bound becomes 1 + the
+ * largest result id (section 3.4.1; 1 if none).
+ *
+ * status[n_modules]: the module's status; err_row[n_modules]: the
+ * module-local index of the instruction the status refers to, -1 for header
+ * and module-level errors and for SPV_OK. With validate == 0 only header and
+ * framing errors are reported.
+ */
+int spv_process_batch(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row,
+                      int validate, uint32_t *out_words, int recompute_bound,
+                      void *workspace, size_t workspace_bytes, int64_t arena_words,
+                      const spv_config *cfg, spv_stream_t stream);
+
+/* spv_decode_batch -- spv_process_batch with validate = 0 and no encode. */
+int spv_decode_batch(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row,
+                     void *workspace, size_t workspace_bytes, const spv_config *cfg, spv_stream_t stream);
+
+/* spv_validate_batch -- validate modules from an already decoded table
+ * (section 3.4.5 rules and section 3.4.2 id rules over the table's rows; the
+ * operand words are read from batch.words at each row's offset). The table
+ * must come from a decode of the same batch; its rows may have been edited
+ * as long as every row still lies inside its module. Writes status/err_row
+ * as spv_process_batch with validate = 1 (framing errors come from the
+ * table: a module whose rows end before its last word is reported as the
+ * decode reported it). */
+int spv_validate_batch(const spv_batch *batch, const spv_table *table, uint32_t *status, int64_t *err_row,
+                       void *workspace, size_t workspace_bytes, int64_t arena_words, spv_stream_t stream);
+
+/* spv_encode_batch -- write out_words[n_words] from a table over the source
+ * words (section 3.2.1 "write"; bound per section 3.4.1). out_words starts as
+ * a copy of the source; for every module with a valid header and every row
+ * of it, the row's first word becomes (wc << 16) | op and, when the opcode
+ * has them, its result type / result id words take the row's rtype / rid;
+ * with recompute_bound the header bound becomes 1 + the largest rid of the
+ * module's rows (1 if none). The table may be edited between decode and
+ * encode; rows must stay inside their module. No workspace. */
+int spv_encode_batch(const spv_batch *src, const spv_table *table, uint32_t *out_words,
+                     int recompute_bound, spv_stream_t stream);
+
+/* Disassembly options (Listing 10): inline_names prints ids as
+ * %<name>_<id> using each id's first OpName; header prints the five header
+ * fields as comment lines first. */
+typedef struct spv_dis_opts {
+    int32_t inline_names;
+    int32_t header;
+} spv_dis_opts;
+
+/* Workspace bytes for spv_disassemble_batch. arena_words is the capacity,
+ * in 32-bit words, of the per-module id tables (first OpName and first
+ * definition of each id): 2 * bound words when bound <= 2 * len + 64, else a
+ * hash map of 3 * (len + 64) words. 0 selects the default
+ * 4 * n_words + 192 * n_modules + 64, which always fits every module. */
+size_t spv_dis_workspace_bytes(int32_t n_modules, int64_t n_words, int64_t n_rows_capacity, int64_t arena_words);
+
+/*
+ * spv_disassemble_batch -- text of every module (section 3.4.4), two passes:
+ * per-instruction length, exclusive scan into 64-bit offsets, write.
+ * Module m's text is text[text_off[m] .. text_off[m+1]); text_off has
+ * n_modules + 1 entries (device). If the total exceeds text_capacity nothing
+ * is written but text_off is still filled: the caller compares
+ * text_off[n_modules] with the capacity after the stream completes and calls
+ * again with a larger buffer. A module with a header error has no text; a
+ * module whose id tables do not fit the arena gets status SPV_CAPACITY in
+ * dis_status (device, n_modules entries, may be NULL) and no text.
+ * The text form: optional "; SPIR-V", "; Version: M.m",
+ * "; Generator: 0x%08x", "; Bound: B", "; Schema: S" lines; then one line
+ * per row: "[%R = ]OpName[ operands]" with the result type first; ids %<id>
+ * or %<name>_<id> (name bytes outside [A-Za-z0-9_] become '_'); literals in
+ * unsigned decimal; strings quoted with \" \\ \xhh escapes; enumerants by
+ * name (bit enums A|B, 0 as None, unknown values in decimal); float
+ * constants as C99 "%a" hexadecimal floating point; rows with an unknown
+ * opcode as Op<decimal> and rows whose operands do not parse as the opcode
+ * name, followed by the remaining words as 0x%08x.
+ */
+int spv_disassemble_batch(const spv_batch *batch, const spv_table *table, const spv_dis_opts *opts,
+                          char *text, uint64_t text_capacity, uint64_t *text_off, uint32_t *dis_status,
+                          void *workspace, size_t workspace_bytes, int64_t arena_words, spv_stream_t stream);
+
+/* Host-side queries of the library's own opcode / enumerant tables (no GPU
+ * needed). spv_op_info returns 0 and fills the outputs for a known opcode,
+ * -1 otherwise; cap is the capability the opcode requires or -1. */
+int spv_op_info(uint32_t opcode, int *has_rtype, int *has_rid, int *cap, const char **name);
+/* kind is one of the enumeration names used by the operand lists
+ * ("Capability", "Decoration", ...). Returns 0 for a known enumerant. */
+int spv_enum_info(const char *kind, uint32_t value, const char **name, int *cap);
+/* Library version string. */
+const char *spv_version(void);
+
+/* Per-kernel timing of the library's own launches, for benchmarks and
+ * profiling (no counterpart in the paper). With profiling on, every launch
+ * made by the calls above is bracketed by two CUDA events recorded on the
+ * launching stream; do not enable it while a stream is being captured.
+ * spv_profile_enable(1) clears the record and starts recording,
+ * spv_profile_enable(0) stops. spv_profile_read waits for the recorded
+ * events, then fills up to max entries (host arrays) with each kernel's name
+ * (static strings), launch count and total milliseconds, and returns the
+ * number of kernels (or a negative SPV_E_* code). */
+int spv_profile_enable(int on);
+int spv_profile_read(int max, const char **names, int64_t *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPV_H */

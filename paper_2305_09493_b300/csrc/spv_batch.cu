@@ -1,0 +1,1064 @@
+// spv_batch.cu -- batched decode / validate / encode of SPIR-V modules.
+//
+// One persistent launch processes every module of a batch, split into tiles
+// of T words (a module owns ceil(len / T) tiles, at least one). Each CTA
+// claims tiles in order from an atomic counter and, per tile:
+//   1. stages the tile (+ a halo) into shared memory with coalesced loads;
+//   2. finds instruction starts. Starts form a chain p -> p + wc(p) from
+//      word 5 of the module (section 3.4.6: instructions are word-counted
+//      32-bit word sequences). Each thread owns a 16-word segment and
+//      computes, backwards, for every position the first chain position past
+//      its segment (or "dead"); each warp then walks 32 candidate entries
+//      through its 512 words; warp 0 composes the warp maps into the tile's
+//      map for 32 candidate entry positions and publishes it. The tile's true
+//      entry comes from a decoupled look-back: the nearest predecessor that
+//      has published its exit, then the predecessors' maps applied in order.
+//      Waits are bounded (max_spins) and end in SPV_TIMEOUT, never a hang.
+//   3. marks starts per segment, counts them and gets the tile's global row
+//      base from a second decoupled look-back (sum of predecessors' counts);
+//   4. writes one structure-of-arrays row per instruction, validates it
+//      (section 3.4.5 rules; ids below the bound and each result id set once,
+//      section 3.4.2) into per-tile aggregates, and re-encodes the tile.
+// A prepass reads headers and lays out tiles and id bitmaps; a finalize pass
+// turns per-module aggregates into status codes; an exact fixup pass runs
+// only for modules with a duplicate result id or a missing capability.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+#include <vector>
+#include <algorithm>
+
+#include "../../include/spv.h"
+#include "spv_device.cuh"
+#include "spv_prof.h"
+
+using namespace spvd;
+
+namespace {
+
+constexpr int HALO = 64;          // words staged past the tile end
+constexpr int NCAND = 32;         // candidate entries in a tile map
+constexpr uint16_t NONE16 = 0xFFFF;
+constexpr unsigned long long F_MAP = 1ull << 62, F_EXIT = 2ull << 62, F_MASK = 3ull << 62;
+
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }   // one spare word per 16: conflict-free segments
+
+struct Params {
+    const uint32_t *words;
+    const int64_t *mod_off;
+    int32_t n_modules;
+    // table
+    uint16_t *op; uint16_t *wc; uint64_t *off; uint32_t *rtype; uint32_t *rid; uint32_t *mod;
+    int64_t *first_row; uint32_t *n_instr; int64_t cap_rows;
+    uint32_t *status; int64_t *err_row;
+    uint32_t *out;                 // encode target or null
+    int validate, recompute_bound;
+    // workspace
+    Ctrl *ctrl; int64_t *tile_off; uint32_t *tile_mod; unsigned long long *tstate; uint32_t *tmap;
+    unsigned long long *cstate; ModState *ms; uint32_t *arena; int64_t arena_words; uint32_t *fixlist;
+    long long max_spins;
+    long long stall_tile;          // test hook: this tile never publishes its look-back states (-1: none)
+    int persistent;
+    int table_mode;                // validating a caller's table: never write its columns
+};
+
+// ---------------------------------------------------------------------------
+// prepass: headers, tile layout and id-bitmap layout (one CTA of 1024 threads)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_prepass(Params P, int tile_words)
+{
+    __shared__ unsigned long long s_tiles[32], s_arena[32];
+    __shared__ unsigned long long s_base_tiles, s_base_arena;
+    int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) { s_base_tiles = 0; s_base_arena = 0; }
+    __syncthreads();
+    for (int base = 0; base < P.n_modules; base += 1024) {
+        int m = base + tid;
+        unsigned long long nt = 0, nb = 0;
+        uint32_t hdr = S_OK, bound = 0, flags = 0;
+        if (m < P.n_modules) {
+            long long o = P.mod_off[m], len = P.mod_off[m + 1] - o;
+            if (len < 0 || len > 0x7fffffffLL) { hdr = S_CAPACITY; flags = MF_CAPACITY; len = 0; }
+            else hdr = header_status(P.words + o, len);
+            if (len >= 4) bound = P.words[o + 3];
+            nt = len > 0 ? (unsigned long long)((len + tile_words - 1) / tile_words) : 1;
+            if (hdr == S_OK && P.validate) nb = idset_words(bound, len);
+        }
+        // block exclusive scan of (nt, nb)
+        unsigned long long it = nt, ib = nb;
+        for (int d = 1; d < 32; d <<= 1) {
+            unsigned long long a = __shfl_up_sync(0xffffffffu, it, d), b = __shfl_up_sync(0xffffffffu, ib, d);
+            if (lane >= d) { it += a; ib += b; }
+        }
+        if (lane == 31) { s_tiles[wid] = it; s_arena[wid] = ib; }
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long a = s_tiles[lane], b = s_arena[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                unsigned long long x = __shfl_up_sync(0xffffffffu, a, d), y = __shfl_up_sync(0xffffffffu, b, d);
+                if (lane >= d) { a += x; b += y; }
+            }
+            s_tiles[lane] = a; s_arena[lane] = b;
+        }
+        __syncthreads();
+        unsigned long long wt = wid ? s_tiles[wid - 1] : 0, wb = wid ? s_arena[wid - 1] : 0;
+        unsigned long long et = s_base_tiles + wt + it - nt, eb = s_base_arena + wb + ib - nb;
+        if (m < P.n_modules) {
+            P.tile_off[m] = (int64_t)et;
+            ModState s;
+            s.hdr = hdr; s.bound = bound; s.err_key = NO_KEY;
+            s.n_cap = s.n_mm = s.n_ep = s.n_fn = 0;
+            s.decl_lo = s.decl_hi = s.req_lo = s.req_hi = 0;
+            s.max_rid = 0;
+            s.arena_off = -1;
+            s.id_slots = 0; s.pad2 = 0;
+            if (hdr == S_OK && P.validate && !idset_dense(bound, P.mod_off[m + 1] - P.mod_off[m]))
+                s.id_slots = (uint32_t)nb;
+            if (hdr == S_OK && P.validate) {
+                if ((long long)(eb + nb) <= P.arena_words) s.arena_off = (long long)eb;
+                else flags |= MF_NOARENA | MF_CAPACITY;
+            }
+            s.flags = flags;
+            P.ms[m] = s;
+        }
+        __syncthreads();
+        if (tid == 1023) { s_base_tiles = et + nt; s_base_arena = eb + nb; }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        P.tile_off[P.n_modules] = (int64_t)s_base_tiles;
+        P.ctrl->n_tiles = s_base_tiles;
+        P.ctrl->arena_used = s_base_arena < (unsigned long long)P.arena_words ? s_base_arena
+                                                                              : (unsigned long long)P.arena_words;
+        P.ctrl->next_tile = 0;
+        P.ctrl->timeout = 0;
+        P.ctrl->total_rows = 0;
+        P.ctrl->n_fix = 0;
+    }
+}
+
+// per tile: owning module, cleared look-back states; clears the id arena
+__global__ void k_tiles(Params P)
+{
+    unsigned long long nt = P.ctrl->n_tiles;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < (long long)nt; g += stride) {
+        int lo = 0, hi = P.n_modules;              // last m with tile_off[m] <= g
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (P.tile_off[mid] <= g) lo = mid; else hi = mid;
+        }
+        P.tile_mod[g] = (uint32_t)lo;
+        P.tstate[g] = 0;
+        P.cstate[g] = 0;
+    }
+    if (P.validate) {
+        unsigned long long aw = P.ctrl->arena_used;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)aw; i += stride)
+            P.arena[i] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the fused tile kernel
+// ---------------------------------------------------------------------------
+template <int NT, int L>
+struct TileSmem {
+    static constexpr int T = NT * L;
+    static constexpr int NW = NT / 32;
+    uint32_t w[(T + HALO) + (T + HALO) / 16 + 1];   // staged words, padded
+    uint32_t E[T + T / 16 + 1];                     // per position: first chain position past its segment
+    uint32_t wmap[NW][32];                          // per warp: exit for its 32 candidate entries
+    uint32_t warp_entry[NW];
+    uint16_t seg_entry[NT];
+    uint32_t warp_tot[NW];
+    // tile scalars
+    long long tile;
+    int m;
+    uint32_t k, len_rel, tile_n, hdr;
+    long long mod_base;
+    uint32_t entry, exitp;
+    unsigned long long row_base;
+    unsigned int count;
+    int timeout;
+    // aggregates flushed once per tile
+    unsigned long long err_key;
+    uint32_t n_cap, n_mm, n_ep, n_fn, decl_lo, decl_hi, req_lo, req_hi, max_rid, flags;
+};
+
+template <int NT, int L>
+__global__ void __launch_bounds__(NT) k_tile(Params P)
+{
+    using S = TileSmem<NT, L>;
+    constexpr int T = S::T;
+    constexpr int NW = S::NW;
+    constexpr int WSPAN = 32 * L;                  // words per warp segment
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S &s = *reinterpret_cast<S *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const spvt::Tables &TB = g_spv_tables;
+
+    for (;;) {
+        if (tid == 0) {
+            s.tile = (long long)atomicAdd(&P.ctrl->next_tile, 1u);
+        }
+        __syncthreads();
+        const long long g = s.tile;
+        if (g >= (long long)P.ctrl->n_tiles) break;
+        if (tid == 0) {
+            int m = (int)P.tile_mod[g];
+            long long first = P.tile_off[m];
+            long long base = P.mod_off[m];
+            long long len = P.mod_off[m + 1] - base;
+            uint32_t k = (uint32_t)(g - first);
+            s.m = m; s.k = k; s.mod_base = base;
+            s.hdr = P.ms[m].hdr;
+            long long lr = len - (long long)k * T;
+            if (s.hdr == S_CAPACITY) lr = 0;
+            s.len_rel = (uint32_t)(lr < 0 ? 0 : lr);
+            s.tile_n = s.len_rel < (uint32_t)T ? s.len_rel : (uint32_t)T;
+            s.timeout = 0;
+            s.err_key = NO_KEY;
+            s.n_cap = s.n_mm = s.n_ep = s.n_fn = 0;
+            s.decl_lo = s.decl_hi = s.req_lo = s.req_hi = 0;
+            s.max_rid = 0; s.flags = 0;
+        }
+        __syncthreads();
+        const uint32_t len_rel = s.len_rel, tile_n = s.tile_n, k = s.k;
+        const int m = s.m;
+        const bool live = (s.hdr == S_OK);
+        const uint32_t *src = P.words + s.mod_base + (long long)k * T;
+
+        // 1. stage
+        {
+            int nload = (int)(len_rel < (uint32_t)(T + HALO) ? len_rel : (uint32_t)(T + HALO));
+            if (!live) nload = 0;
+            #pragma unroll 4
+            for (int i = tid; i < T + HALO; i += NT) s.w[pad(i)] = i < nload ? __ldg(src + i) : 0u;
+        }
+        __syncthreads();
+        auto word = [&](uint32_t p) -> uint32_t { return p < (uint32_t)(T + HALO) ? s.w[pad((int)p)] : __ldg(src + p); };
+
+        // 2a. per-segment exits (backwards dynamic programming)
+        {
+            int lo = tid * L;
+            int hi = lo + L;
+            if (hi > (int)tile_n) hi = (int)tile_n;
+            for (int q = hi - 1; q >= lo; q--) {
+                uint32_t wc = s.w[pad(q)] >> 16;
+                uint32_t e;
+                if (wc == 0 || (uint32_t)q + wc > len_rel) e = DEAD;
+                else if (q + (int)wc >= hi) e = (uint32_t)q + wc;
+                else e = s.E[pad(q + (int)wc)];
+                s.E[pad(q)] = e;
+            }
+        }
+        __syncthreads();
+        // 2b. per warp: exits of the 32 candidate entries at the start of its segment
+        {
+            uint32_t wb = (uint32_t)wid * WSPAN;
+            uint32_t we = wb + WSPAN < tile_n ? wb + WSPAN : tile_n;
+            uint32_t x = wb + lane;
+            while (x < we) { x = s.E[pad((int)x)]; if (x == DEAD) break; }
+            s.wmap[wid][lane] = x;
+        }
+        __syncthreads();
+        // 2c. warp 0: tile map for entries 0..31, publish, look back for the entry
+        if (wid == 0) {
+            uint32_t x = s.wmap[0][lane];
+            for (int w2 = 1; w2 < NW; w2++) {
+                if (x == DEAD || x >= tile_n) break;
+                uint32_t wb = (uint32_t)w2 * WSPAN;
+                if (x - wb < 32) x = s.wmap[w2][x - wb];
+                else if (x < wb + WSPAN) { x = UNRES; break; }
+            }
+            uint32_t mv = (x == DEAD || x == UNRES) ? x : x + k * (uint32_t)T;
+            long long first = g - (long long)k;
+            const bool stalled = (g == P.stall_tile);
+            bool need_lookback = live && k > 0;
+            if (need_lookback && !stalled) {
+                P.tmap[g * NCAND + lane] = mv;
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) st_release(&P.tstate[g], F_MAP);
+            }
+            // entry of this tile (module-relative)
+            uint32_t entry;
+            if (!live) entry = DEAD;
+            else if (k == 0) entry = 5;
+            else {
+                // find the nearest predecessor with a published exit
+                long long hi_j = g - 1;
+                long long spins = 0;
+                long long anchor = -1;
+                uint32_t ax = DEAD;
+                bool gave_up = false;
+                for (;;) {
+                    long long j = hi_j - lane;
+                    unsigned long long st = j >= first ? ld_acquire(&P.tstate[j]) : F_EXIT;
+                    unsigned long long f = st & F_MASK;
+                    unsigned exitm = __ballot_sync(0xffffffffu, j < first || f == F_EXIT);
+                    unsigned nonem = __ballot_sync(0xffffffffu, j >= first && f == 0);
+                    if (exitm) {
+                        int le = __ffs(exitm) - 1;
+                        if (nonem & ((1u << le) - 1u)) {
+                            if (++spins > P.max_spins) { gave_up = true; break; }
+                            spin_pause();
+                            continue;
+                        }
+                        unsigned long long sv = __shfl_sync(0xffffffffu, st, le);
+                        anchor = hi_j - le;
+                        ax = anchor < first ? 5u : (uint32_t)(sv & 0xffffffffu);
+                        break;
+                    }
+                    if (nonem) {
+                        if (++spins > P.max_spins) { gave_up = true; break; }
+                        spin_pause();
+                        continue;
+                    }
+                    hi_j -= 32;
+                }
+                // apply predecessors' maps from the anchor forward
+                uint32_t xx = ax;
+                for (long long t = anchor + 1; t < g && !gave_up; t += 8) {
+                    uint32_t mrow[8];
+                    #pragma unroll
+                    for (int q = 0; q < 8; q++) mrow[q] = (t + q < g) ? P.tmap[(t + q) * NCAND + lane] : 0u;
+                    #pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        long long tt = t + q;
+                        if (tt >= g) break;
+                        uint32_t kt = (uint32_t)(tt - first);
+                        uint32_t tb = kt * (uint32_t)T;
+                        uint32_t val = __shfl_sync(0xffffffffu, mrow[q], (int)((xx - tb) & 31u));
+                        if (xx == DEAD || xx >= tb + (uint32_t)T) continue;
+                        if (xx - tb < 32 && val != UNRES) { xx = val; continue; }
+                        // the map cannot tell: wait for this tile's own exit
+                        unsigned long long st;
+                        for (;;) {
+                            st = 0;
+                            if (lane == 0) st = ld_acquire(&P.tstate[tt]);
+                            st = __shfl_sync(0xffffffffu, st, 0);
+                            if ((st & F_MASK) == F_EXIT) break;
+                            if (++spins > P.max_spins) { gave_up = true; break; }
+                            spin_pause();
+                        }
+                        if (gave_up) break;
+                        xx = (uint32_t)(st & 0xffffffffu);
+                    }
+                }
+                entry = gave_up ? DEAD : xx;
+                if (gave_up && lane == 0) s.timeout = 1;
+            }
+            // 2d. compose through the warp segments for the true entry
+            if (lane == 0) {
+                uint32_t x0 = (entry == DEAD) ? DEAD : (entry >= k * (uint32_t)T ? entry - k * (uint32_t)T : DEAD);
+                uint32_t xw = x0;
+                for (int w2 = 0; w2 < NW; w2++) {
+                    uint32_t wb = (uint32_t)w2 * WSPAN;
+                    uint32_t we = wb + WSPAN < tile_n ? wb + WSPAN : tile_n;
+                    if (xw == DEAD || xw >= tile_n || xw >= we) { s.warp_entry[w2] = DEAD; continue; }
+                    s.warp_entry[w2] = xw;
+                    if (xw - wb < 32) xw = s.wmap[w2][xw - wb];
+                    else { while (xw < we) { xw = s.E[pad((int)xw)]; if (xw == DEAD) break; } }
+                }
+                s.entry = x0;
+                s.exitp = xw;
+                if (live && g != P.stall_tile) {
+                    uint32_t mx = xw == DEAD ? DEAD : xw + k * (uint32_t)T;
+                    __threadfence();
+                    st_release(&P.tstate[g], F_EXIT | (unsigned long long)mx);
+                }
+            }
+        }
+        __syncthreads();
+        // 2e. per warp: entry of each 16-word segment (serial walk by lane 0)
+        s.seg_entry[tid] = NONE16;
+        __syncwarp();
+        if (lane == 0) {
+            uint32_t x = s.warp_entry[wid];
+            uint32_t wb = (uint32_t)wid * WSPAN;
+            uint32_t we = wb + WSPAN < tile_n ? wb + WSPAN : tile_n;
+            while (x != DEAD && x < we) {
+                s.seg_entry[x / L] = (uint16_t)x;
+                x = s.E[pad((int)x)];
+            }
+        }
+        __syncthreads();
+        // 3. mark starts in my segment; detect the framing error if the chain dies here
+        uint32_t mask = 0;
+        int ferr = -1;          // 0 zero word count, 1 truncated
+        {
+            int lo = tid * L;
+            int hi = lo + L < (int)tile_n ? lo + L : (int)tile_n;
+            uint32_t p = s.seg_entry[tid];
+            if (p != NONE16) {
+                while ((int)p < hi) {
+                    uint32_t wc = s.w[pad((int)p)] >> 16;
+                    if (wc == 0) { ferr = 0; break; }
+                    if (p + wc > len_rel) { ferr = 1; break; }
+                    mask |= 1u << (p - lo);
+                    p += wc;
+                }
+            }
+        }
+        const unsigned cnt = __popc(mask);
+        unsigned incl = cnt;
+        #pragma unroll
+        for (int d = 1; d < 32; d <<= 1) { unsigned v = __shfl_up_sync(0xffffffffu, incl, d); if (lane >= d) incl += v; }
+        if (lane == 31) s.warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned v = lane < NW ? s.warp_tot[lane] : 0;
+            #pragma unroll
+            for (int d = 1; d < 32; d <<= 1) { unsigned u = __shfl_up_sync(0xffffffffu, v, d); if (lane >= d) v += u; }
+            if (lane < NW) s.warp_tot[lane] = v;
+            unsigned total = __shfl_sync(0xffffffffu, v, NW - 1);
+            // 3b. row base from the predecessors' counts (decoupled look-back over all tiles)
+            unsigned long long excl = 0;
+            const bool stalled = (g == P.stall_tile);
+            if (g == 0) {
+                if (lane == 0 && !stalled) st_release(&P.cstate[0], F_EXIT | total);
+            } else {
+                if (lane == 0 && !stalled) st_release(&P.cstate[g], F_MAP | total);
+                long long hi_j = g - 1;
+                long long spins = 0;
+                bool gave_up = false;
+                for (;;) {
+                    long long j = hi_j - lane;
+                    unsigned long long st = j >= 0 ? ld_acquire(&P.cstate[j]) : F_EXIT;
+                    unsigned long long f = st & F_MASK;
+                    unsigned exitm = __ballot_sync(0xffffffffu, f == F_EXIT);
+                    unsigned nonem = __ballot_sync(0xffffffffu, f == 0);
+                    int le = exitm ? __ffs(exitm) - 1 : 32;
+                    unsigned below = le == 32 ? 0xffffffffu : ((1u << le) - 1u);
+                    if (nonem & below) {
+                        if (++spins > P.max_spins) { gave_up = true; break; }
+                        spin_pause();
+                        continue;
+                    }
+                    unsigned long long v = (lane <= le && j >= 0) ? (st & ~F_MASK) : 0ull;
+                    #pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+                    excl += v;
+                    if (exitm) break;
+                    hi_j -= 32;
+                }
+                if (gave_up) { excl = 0; if (lane == 0) s.timeout = 1; }
+                if (lane == 0 && !stalled) st_release(&P.cstate[g], F_EXIT | (excl + total));
+            }
+            if (lane == 0) {
+                s.row_base = excl;
+                s.count = total;
+                if (k == 0) P.first_row[m] = (int64_t)excl;
+                if (g == (long long)P.ctrl->n_tiles - 1) P.ctrl->total_rows = excl + total;
+            }
+        }
+        __syncthreads();
+        const unsigned long long row_base = s.row_base;
+        const unsigned tile_count = s.count;
+        const unsigned my_off = (wid ? s.warp_tot[wid - 1] : 0) + incl - cnt;
+        if (ferr >= 0 && live) {
+            unsigned long long key = make_key(row_base + my_off + cnt, R_FRAME, (uint32_t)ferr);
+            atomicMin(&s.err_key, key);
+        }
+        // 4. start list (reuses E), then one row per thread
+        uint16_t *S16 = reinterpret_cast<uint16_t *>(s.E);
+        {
+            uint32_t x = mask;
+            unsigned o = my_off;
+            while (x) { int b = __ffs(x) - 1; x &= x - 1; S16[o++] = (uint16_t)(tid * L + b); }
+        }
+        __syncthreads();
+        const uint32_t bound = P.ms[m].bound;
+        const long long arena_off = P.validate ? P.ms[m].arena_off : -1;
+        const uint32_t id_slots = P.ms[m].id_slots;
+        for (unsigned r = tid; r < tile_count; r += NT) {
+            uint32_t p = S16[r];
+            uint32_t w0 = word(p);
+            uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
+            const spvt::OpDesc &d = TB.ops[op < 256 ? op : 0];
+            bool known = op < 256 && (d.flags & 1);
+            uint32_t rt = 0, ri = 0;
+            if (known) {
+                uint32_t q = 1;
+                if (d.flags & 2) { if (q < wc) rt = word(p + q); q++; }
+                if (d.flags & 4) { if (q < wc) ri = word(p + q); }
+            }
+            unsigned long long row = row_base + r;
+            if ((long long)row < P.cap_rows) {
+                P.op[row] = (uint16_t)op; P.wc[row] = (uint16_t)wc;
+                P.off[row] = (uint64_t)(s.mod_base + (long long)k * T + p);
+                P.rtype[row] = rt; P.rid[row] = ri; P.mod[row] = (uint32_t)m;
+            } else {
+                atomicOr(&s.flags, MF_CAPACITY);
+            }
+            if (ri > 0) atomicMax(&s.max_rid, ri);
+            if (P.validate) {
+                if (op == 17) { atomicAdd(&s.n_cap, 1u); if (wc >= 2) { uint32_t c = word(p + 1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); } }
+                else if (op == 14) atomicAdd(&s.n_mm, 1u);
+                else if (op == 15) atomicAdd(&s.n_ep, 1u);
+                else if (op == 54) atomicAdd(&s.n_fn, 1u);
+                if (!known) { atomicMin(&s.err_key, make_key(row, R_UNKNOWN, 0)); }
+                else {
+                    auto iw = [&](uint32_t i) -> uint32_t { return word(p + i); };
+                    Walk wk = walk_instruction(iw, wc, d, bound);
+                    if (!wk.ok) atomicMin(&s.err_key, make_key(row, R_BADOP, 0));
+                    else if (wk.oob) atomicMin(&s.err_key, make_key(row, R_OOB, 0));
+                    else {
+                        if ((d.flags & 4) && arena_off >= 0 && idset_insert(P.arena + arena_off, id_slots, ri))
+                            atomicOr(&s.flags, MF_DUP);
+                        uint64_t req = wk.req | width_caps(iw, op, wc);
+                        if (req) {
+                            if ((uint32_t)req) atomicOr(&s.req_lo, (uint32_t)req);
+                            if ((uint32_t)(req >> 32)) atomicOr(&s.req_hi, (uint32_t)(req >> 32));
+                        }
+                    }
+                }
+            }
+        }
+        // 5. encode. In the fused path every field an instruction writes back
+        // (first word from wc/op, result type, result id) was just decoded from
+        // the staged words themselves, so the re-encoded tile is the staged
+        // tile; the header bound is patched by the finalize pass.
+        if (P.out) {
+            uint32_t *dst = P.out + s.mod_base + (long long)k * T;
+            int n = live ? (int)tile_n : (int)(len_rel < (uint32_t)T ? len_rel : (uint32_t)T);
+            if (live) {
+                for (int i = tid; i < n; i += NT) dst[i] = s.w[pad(i)];
+            } else {
+                for (int i = tid; i < n; i += NT) dst[i] = __ldg(src + i);
+            }
+        }
+        __syncthreads();
+        // 6. flush the tile's aggregates to the module
+        if (tid == 0) {
+            ModState *ms = &P.ms[m];
+            if (s.err_key != NO_KEY) atomicMin(&ms->err_key, s.err_key);
+            if (s.n_cap) atomicAdd(&ms->n_cap, s.n_cap);
+            if (s.n_mm) atomicAdd(&ms->n_mm, s.n_mm);
+            if (s.n_ep) atomicAdd(&ms->n_ep, s.n_ep);
+            if (s.n_fn) atomicAdd(&ms->n_fn, s.n_fn);
+            if (s.decl_lo) atomicOr(&ms->decl_lo, s.decl_lo);
+            if (s.decl_hi) atomicOr(&ms->decl_hi, s.decl_hi);
+            if (s.req_lo) atomicOr(&ms->req_lo, s.req_lo);
+            if (s.req_hi) atomicOr(&ms->req_hi, s.req_hi);
+            if (s.max_rid) atomicMax(&ms->max_rid, s.max_rid);
+            uint32_t fl = s.flags | (s.timeout ? MF_TIMEOUT : 0u);
+            if (fl) atomicOr(&ms->flags, fl);
+            if (s.timeout) atomicExch(&P.ctrl->timeout, 1u);
+        }
+        if (!P.persistent) break;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// finalize: per module status, row counts, bound of the encoded header
+// ---------------------------------------------------------------------------
+__device__ void module_status(const Params &P, int m, unsigned long long key, uint32_t *st, int64_t *er)
+{
+    const ModState &s = P.ms[m];
+    int64_t first = P.first_row[m];
+    if (P.ctrl->timeout || (s.flags & MF_TIMEOUT)) { *st = S_TIMEOUT; *er = -1; return; }
+    if (s.hdr != S_OK) { *st = s.hdr; *er = -1; return; }
+    if (s.flags & MF_CAPACITY) { *st = S_CAPACITY; *er = -1; return; }
+    if (key != NO_KEY) {
+        uint32_t code = key_status(key);
+        *st = code;
+        *er = (int64_t)(key >> 8) - first;
+        return;
+    }
+    *er = -1;
+    if (!P.validate) { *st = S_OK; return; }
+    if (s.n_cap == 0) *st = S_NO_CAPABILITY;
+    else if (s.n_mm == 0) *st = S_NO_MEMORY_MODEL;
+    else if (s.n_mm > 1) *st = S_MULTI_MEMORY_MODEL;
+    else if (s.n_ep == 0) *st = S_NO_ENTRY_POINT;
+    else if (s.n_fn == 0) *st = S_NO_FUNCTION;
+    else *st = S_OK;
+}
+
+__global__ void k_finalize(Params P)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= P.n_modules) return;
+    if (!P.table_mode) {
+        unsigned long long total = P.ctrl->total_rows;
+        int64_t first = P.first_row[m];
+        int64_t next = m + 1 < P.n_modules ? P.first_row[m + 1] : (int64_t)total;
+        P.n_instr[m] = (uint32_t)(next - first);
+        if (m == P.n_modules - 1) P.first_row[P.n_modules] = (int64_t)total;
+    }
+    ModState &s = P.ms[m];
+    if (P.out && P.recompute_bound && s.hdr == S_OK) P.out[P.mod_off[m] + 3] = s.max_rid + 1;
+    if (P.validate && s.hdr == S_OK && !(s.flags & (MF_CAPACITY | MF_TIMEOUT)) && !P.ctrl->timeout) {
+        uint64_t decl = ((uint64_t)s.decl_hi << 32) | s.decl_lo;
+        uint64_t req = ((uint64_t)s.req_hi << 32) | s.req_lo;
+        uint64_t missing = req & ~cap_closure(decl);
+        if (missing || (s.flags & MF_DUP)) {
+            s.flags |= MF_FIXUP;
+            unsigned slot = atomicAdd(&P.ctrl->n_fix, 1u);
+            P.fixlist[slot] = (uint32_t)m;
+            return;
+        }
+    }
+    uint32_t st; int64_t er;
+    module_status(P, m, s.err_key, &st, &er);
+    P.status[m] = st;
+    P.err_row[m] = er;
+}
+
+// ---------------------------------------------------------------------------
+// exact fixup for the few modules with a missing capability or a duplicate
+// result id: one CTA per module, over its table rows.
+//   missing capability: min row (passing the earlier checks) requiring a
+//     capability outside the closure of the declared ones;
+//   duplicate: min row r whose result id some row < r already defines --
+//     rows are taken in order, chunk by chunk: a row is a duplicate if the
+//     id bitmap (rows of earlier chunks) has its id, or a lower row of the
+//     same chunk has it (shared-memory hash of the chunk's ids).
+// ---------------------------------------------------------------------------
+constexpr int FIX_NT = 512;
+constexpr int FIX_CHUNK = 2048;
+constexpr int FIX_HASH = 4096;
+
+__global__ void __launch_bounds__(FIX_NT) k_fixup(Params P)
+{
+    __shared__ unsigned long long s_best;
+    __shared__ uint32_t h_key[FIX_HASH];
+    __shared__ uint32_t h_min[FIX_HASH];
+    __shared__ int s_stop;
+    const spvt::Tables &TB = g_spv_tables;
+    unsigned n_fix = P.ctrl->n_fix;
+    for (unsigned f = blockIdx.x; f < n_fix; f += gridDim.x) {
+        int m = (int)P.fixlist[f];
+        ModState &ms = P.ms[m];
+        int64_t first = P.first_row[m];
+        int64_t n = P.n_instr[m];
+        uint32_t bound = ms.bound;
+        uint64_t decl = ((uint64_t)ms.decl_hi << 32) | ms.decl_lo;
+        uint64_t req = ((uint64_t)ms.req_hi << 32) | ms.req_lo;
+        uint64_t missing = req & ~cap_closure(decl);
+        if (threadIdx.x == 0) { s_best = ms.err_key; s_stop = 0; }
+        __syncthreads();
+        if (missing) {
+            for (int64_t r = threadIdx.x; r < n; r += FIX_NT) {
+                int64_t row = first + r;
+                uint32_t op = P.op[row], wc = P.wc[row];
+                if (op >= 256 || !(TB.ops[op].flags & 1)) continue;
+                const uint32_t *iwp = P.words + P.off[row];
+                auto iw = [&](uint32_t i) -> uint32_t { return __ldg(iwp + i); };
+                Walk wk = walk_instruction(iw, wc, TB.ops[op], bound);
+                if (!wk.ok) continue;
+                uint64_t rq = wk.req | width_caps(iw, op, wc);
+                if (rq & missing) atomicMin(&s_best, make_key((unsigned long long)row, R_MISSING, 0));
+            }
+        }
+        if ((ms.flags & MF_DUP) && ms.arena_off >= 0) {
+            uint32_t *bm = P.arena + ms.arena_off;
+            const uint32_t slots = ms.id_slots;
+            long long len_m = P.mod_off[m + 1] - P.mod_off[m];
+            unsigned long long nbw = idset_words(bound, len_m);
+            for (unsigned long long i = threadIdx.x; i < nbw; i += FIX_NT) bm[i] = 0;
+            __syncthreads();
+            for (int64_t c0 = 0; c0 < n; c0 += FIX_CHUNK) {
+                for (int i = threadIdx.x; i < FIX_HASH; i += FIX_NT) { h_key[i] = 0; h_min[i] = 0xffffffffu; }
+                __syncthreads();
+                // ids of this chunk's defining rows: first occurrence in the chunk
+                for (int i = threadIdx.x; i < FIX_CHUNK; i += FIX_NT) {
+                    int64_t r = c0 + i;
+                    if (r >= n) break;
+                    int64_t row = first + r;
+                    uint32_t op = P.op[row];
+                    if (op >= 256 || !(TB.ops[op].flags & 4)) continue;
+                    uint32_t id = P.rid[row];
+                    if (id == 0 || id >= bound) continue;
+                    uint32_t h = (id * 2654435761u) & (FIX_HASH - 1);
+                    for (;;) {
+                        uint32_t prev = atomicCAS(&h_key[h], 0u, id);
+                        if (prev == 0 || prev == id) { atomicMin(&h_min[h], (uint32_t)i); break; }
+                        h = (h + 1) & (FIX_HASH - 1);
+                    }
+                }
+                __syncthreads();
+                for (int i = threadIdx.x; i < FIX_CHUNK; i += FIX_NT) {
+                    int64_t r = c0 + i;
+                    if (r >= n) break;
+                    int64_t row = first + r;
+                    uint32_t op = P.op[row];
+                    if (op >= 256 || !(TB.ops[op].flags & 4)) continue;
+                    uint32_t id = P.rid[row];
+                    if (id == 0 || id >= bound) continue;
+                    bool dup = idset_contains(bm, slots, id);
+                    if (!dup) {
+                        uint32_t h = (id * 2654435761u) & (FIX_HASH - 1);
+                        while (h_key[h] != id) h = (h + 1) & (FIX_HASH - 1);
+                        dup = h_min[h] < (uint32_t)i;
+                    }
+                    if (dup) { atomicMin(&s_best, make_key((unsigned long long)row, R_DUP, 0)); s_stop = 1; }
+                }
+                __syncthreads();
+                for (int i = threadIdx.x; i < FIX_CHUNK; i += FIX_NT) {
+                    int64_t r = c0 + i;
+                    if (r >= n) break;
+                    int64_t row = first + r;
+                    uint32_t op = P.op[row];
+                    if (op >= 256 || !(TB.ops[op].flags & 4)) continue;
+                    uint32_t id = P.rid[row];
+                    if (id == 0 || id >= bound) continue;
+                    idset_insert(bm, slots, id);
+                }
+                __syncthreads();
+                if (s_stop) break;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t st; int64_t er;
+            module_status(P, m, s_best, &st, &er);
+            P.status[m] = st;
+            P.err_row[m] = er;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// validate from an existing table
+// ---------------------------------------------------------------------------
+__global__ void k_validate_rows(Params P)
+{
+    const spvt::Tables &TB = g_spv_tables;
+    long long n_rows = P.first_row[P.n_modules];
+    if (n_rows > P.cap_rows) n_rows = P.cap_rows;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < n_rows; row += stride) {
+        uint32_t m = P.mod[row];
+        ModState *ms = &P.ms[m];
+        if (ms->hdr != S_OK) continue;
+        uint32_t op = P.op[row], wc = P.wc[row];
+        const uint32_t *iwp = P.words + P.off[row];
+        auto iw = [&](uint32_t i) -> uint32_t { return __ldg(iwp + i); };
+        uint32_t ri = P.rid[row];
+        if (ri) atomicMax(&ms->max_rid, ri);
+        if (op == 17) { atomicAdd(&ms->n_cap, 1u); if (wc >= 2) { uint32_t c = iw(1); if (c < 32) atomicOr(&ms->decl_lo, 1u << c); else if (c < 64) atomicOr(&ms->decl_hi, 1u << (c - 32)); } }
+        else if (op == 14) atomicAdd(&ms->n_mm, 1u);
+        else if (op == 15) atomicAdd(&ms->n_ep, 1u);
+        else if (op == 54) atomicAdd(&ms->n_fn, 1u);
+        if (op >= 256 || !(TB.ops[op].flags & 1)) { atomicMin(&ms->err_key, make_key((unsigned long long)row, R_UNKNOWN, 0)); continue; }
+        const spvt::OpDesc &d = TB.ops[op];
+        Walk wk = walk_instruction(iw, wc, d, ms->bound);
+        if (!wk.ok) { atomicMin(&ms->err_key, make_key((unsigned long long)row, R_BADOP, 0)); continue; }
+        if (wk.oob) { atomicMin(&ms->err_key, make_key((unsigned long long)row, R_OOB, 0)); continue; }
+        if ((d.flags & 4) && ms->arena_off >= 0 && idset_insert(P.arena + ms->arena_off, ms->id_slots, ri))
+            atomicOr(&ms->flags, MF_DUP);
+        uint64_t req = wk.req | width_caps(iw, op, wc);
+        if ((uint32_t)req) atomicOr(&ms->req_lo, (uint32_t)req);
+        if ((uint32_t)(req >> 32)) atomicOr(&ms->req_hi, (uint32_t)(req >> 32));
+    }
+}
+
+// framing errors of a decoded table: the rows of module m end before the
+// module's last word exactly when decode stopped at a framing error
+__global__ void k_table_framing(Params P)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= P.n_modules) return;
+    ModState &s = P.ms[m];
+    if (s.hdr != S_OK) return;
+    int64_t first = P.first_row[m];
+    uint32_t n = P.n_instr[m];
+    long long base = P.mod_off[m], len = P.mod_off[m + 1] - base;
+    long long endp = n ? (long long)(P.off[first + n - 1] - base) + P.wc[first + n - 1] : 5;
+    if (endp < len) {
+        uint32_t wc = P.words[base + endp] >> 16;
+        atomicMin(&s.err_key, make_key((unsigned long long)(first + n), R_FRAME, wc == 0 ? 0u : 1u));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// encode from a table
+// ---------------------------------------------------------------------------
+__global__ void k_encode_bound_init(const uint32_t *words, const int64_t *mod_off, int n_mod, uint32_t *out)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_mod) return;
+    long long o = mod_off[m], n = mod_off[m + 1] - o;
+    if (n >= 0 && n <= 0x7fffffffLL && header_status(words + o, n) == S_OK) out[o + 3] = 1;
+}
+
+__global__ void k_encode_rows(const uint32_t *words, const int64_t *mod_off, const uint16_t *op,
+                              const uint16_t *wc, const uint64_t *off, const uint32_t *rtype,
+                              const uint32_t *rid, const uint32_t *mod, const int64_t *first_row,
+                              int n_mod, long long cap_rows, uint32_t *out, int recompute)
+{
+    const spvt::Tables &TB = g_spv_tables;
+    long long n_rows = first_row[n_mod];
+    if (n_rows > cap_rows) n_rows = cap_rows;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n_rows; r += stride) {
+        uint32_t m = mod[r];
+        long long o = mod_off[m], n = mod_off[m + 1] - o;
+        if (n > 0x7fffffffLL || header_status(words + o, n) != S_OK) continue;
+        uint64_t p = off[r];
+        uint32_t c = wc[r], opc = op[r];
+        out[p] = (c << 16) | opc;
+        if (opc < 256 && (TB.ops[opc].flags & 1)) {
+            uint32_t q = 1;
+            if (TB.ops[opc].flags & 2) { if (q < c) out[p + q] = rtype[r]; q++; }
+            if (TB.ops[opc].flags & 4) { if (q < c) out[p + q] = rid[r]; }
+        }
+        if (recompute) atomicMax(&out[o + 3], rid[r] + 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct Layout {
+    size_t ctrl, tile_off, tile_mod, tstate, tmap, cstate, ms, fixlist, arena, total;
+    long long max_tiles, arena_words;
+};
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+Layout make_layout(int n_mod, long long n_words, long long arena_words, int tile_words)
+{
+    Layout L{};
+    L.max_tiles = n_words / tile_words + n_mod + 1;
+    L.arena_words = arena_words > 0 ? arena_words : 2 * n_words + 64LL * n_mod + 64;
+    size_t o = 0;
+    L.ctrl = o; o = al(o + sizeof(Ctrl));
+    L.tile_off = o; o = al(o + 8 * (size_t)(n_mod + 1));
+    L.tile_mod = o; o = al(o + 4 * (size_t)L.max_tiles);
+    L.tstate = o; o = al(o + 8 * (size_t)L.max_tiles);
+    L.tmap = o; o = al(o + 4 * (size_t)NCAND * L.max_tiles);
+    L.cstate = o; o = al(o + 8 * (size_t)L.max_tiles);
+    L.ms = o; o = al(o + sizeof(ModState) * (size_t)n_mod);
+    L.fixlist = o; o = al(o + 4 * (size_t)n_mod);
+    L.arena = o; o = al(o + 4 * (size_t)L.arena_words);
+    L.total = o;
+    return L;
+}
+
+struct Cfg { int T, NT, L, ctas_per_sm, per_module; long long max_spins, stall_tile; };
+
+int resolve_cfg(const spv_config *c, Cfg *out)
+{
+    Cfg r{4096, 256, 16, 0, 0, 1LL << 20, -1};
+    if (c) {
+        if (c->tile_words) r.T = c->tile_words;
+        if (c->threads) r.NT = c->threads;
+        if (c->ctas_per_sm < 0 || c->max_spins < 0 || c->test_stall_tile < 0) return SPV_E_ARG;
+        r.ctas_per_sm = c->ctas_per_sm;
+        r.per_module = c->per_module;
+        if (c->max_spins) r.max_spins = c->max_spins;
+        r.stall_tile = c->test_stall_tile - 1;
+    }
+    if (r.NT != 128 && r.NT != 256) return SPV_E_ARG;
+    if (r.T % r.NT) return SPV_E_ARG;
+    r.L = r.T / r.NT;
+    if (r.L != 8 && r.L != 16) return SPV_E_ARG;
+    *out = r;
+    return 0;
+}
+
+template <int NT, int L>
+int launch_tile_kernel(const Params &P, int grid, cudaStream_t st)
+{
+    size_t sm = sizeof(TileSmem<NT, L>);
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !configured[dev]) {
+        if (cudaFuncSetAttribute(k_tile<NT, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+            return SPV_E_CUDA;
+        configured[dev] = true;
+    }
+    SPV_LAUNCH("k_tile", st, k_tile<NT, L><<<grid, NT, sm, st>>>(P));
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : SPV_E_CUDA;
+}
+
+template <int NT, int L>
+int occupancy(int *per_sm)
+{
+    size_t sm = sizeof(TileSmem<NT, L>);
+    cudaFuncSetAttribute(k_tile<NT, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tile<NT, L>, NT, sm) == cudaSuccess ? 0 : SPV_E_CUDA;
+}
+
+int dispatch_tile(const Params &P, const Cfg &c, int grid, cudaStream_t st)
+{
+    if (c.NT == 256 && c.L == 16) return launch_tile_kernel<256, 16>(P, grid, st);
+    if (c.NT == 256 && c.L == 8) return launch_tile_kernel<256, 8>(P, grid, st);
+    if (c.NT == 128 && c.L == 16) return launch_tile_kernel<128, 16>(P, grid, st);
+    if (c.NT == 128 && c.L == 8) return launch_tile_kernel<128, 8>(P, grid, st);
+    return SPV_E_ARG;
+}
+
+int dispatch_occupancy(const Cfg &c, int *per_sm)
+{
+    if (c.NT == 256 && c.L == 16) return occupancy<256, 16>(per_sm);
+    if (c.NT == 256 && c.L == 8) return occupancy<256, 8>(per_sm);
+    if (c.NT == 128 && c.L == 16) return occupancy<128, 16>(per_sm);
+    if (c.NT == 128 && c.L == 8) return occupancy<128, 8>(per_sm);
+    return SPV_E_ARG;
+}
+
+bool check_batch(const spv_batch *b)
+{
+    return b && b->n_modules >= 0 && b->n_words >= 0 && (b->n_words == 0 || b->words) && b->mod_off;
+}
+
+Params base_params(const spv_batch *b, void *ws, const Layout &L)
+{
+    Params P{};
+    char *w = (char *)ws;
+    P.words = b->words; P.mod_off = b->mod_off; P.n_modules = b->n_modules;
+    P.ctrl = (Ctrl *)(w + L.ctrl);
+    P.tile_off = (int64_t *)(w + L.tile_off);
+    P.tile_mod = (uint32_t *)(w + L.tile_mod);
+    P.tstate = (unsigned long long *)(w + L.tstate);
+    P.tmap = (uint32_t *)(w + L.tmap);
+    P.cstate = (unsigned long long *)(w + L.cstate);
+    P.ms = (ModState *)(w + L.ms);
+    P.fixlist = (uint32_t *)(w + L.fixlist);
+    P.arena = (uint32_t *)(w + L.arena);
+    P.arena_words = L.arena_words;
+    return P;
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" size_t spv_workspace_bytes(int32_t n_modules, int64_t n_words, int64_t arena_words, const spv_config *cfg)
+{
+    Cfg c;
+    if (n_modules < 0 || n_words < 0 || resolve_cfg(cfg, &c)) return 0;
+    return make_layout(n_modules, n_words, arena_words, c.T).total;
+}
+
+extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row,
+                                 int validate, uint32_t *out_words, int recompute_bound, void *workspace,
+                                 size_t workspace_bytes, int64_t arena_words, const spv_config *cfg,
+                                 spv_stream_t stream)
+{
+    Cfg c;
+    if (!check_batch(batch) || !table || !status || !err_row || resolve_cfg(cfg, &c)) return SPV_E_ARG;
+    if (!table->op || !table->wc || !table->off || !table->rtype || !table->rid || !table->mod ||
+        !table->mod_first_row || !table->mod_n_instr || table->capacity_rows < 0)
+        return SPV_E_ARG;
+    Layout L = make_layout(batch->n_modules, batch->n_words, arena_words, c.T);
+    if (!workspace || workspace_bytes < L.total) return SPV_E_WORKSPACE;
+    if (batch->n_modules == 0) return SPV_SUCCESS;
+    cudaStream_t st = (cudaStream_t)stream;
+    Params P = base_params(batch, workspace, L);
+    P.op = table->op; P.wc = table->wc; P.off = table->off; P.rtype = table->rtype; P.rid = table->rid;
+    P.mod = table->mod; P.first_row = table->mod_first_row; P.n_instr = table->mod_n_instr;
+    P.cap_rows = table->capacity_rows;
+    P.status = status; P.err_row = err_row;
+    P.out = out_words; P.validate = validate ? 1 : 0; P.recompute_bound = recompute_bound ? 1 : 0;
+    P.max_spins = c.max_spins;
+    P.stall_tile = c.stall_tile;
+    SPV_LAUNCH("k_prepass", st, k_prepass<<<1, 1024, 0, st>>>(P, c.T));
+    int nsm = sm_count();
+    SPV_LAUNCH("k_tiles", st, k_tiles<<<nsm * 4, 256, 0, st>>>(P));
+    if (cudaPeekAtLastError() != cudaSuccess) return SPV_E_CUDA;
+    int rc;
+    if (!c.per_module) {
+        int per_sm = c.ctas_per_sm;
+        if (per_sm <= 0) { if (dispatch_occupancy(c, &per_sm)) return SPV_E_CUDA; if (per_sm < 1) per_sm = 1; }
+        P.persistent = 1;
+        rc = dispatch_tile(P, c, nsm * per_sm, st);
+    } else {
+        // comparison path: one launch per module, each CTA one tile
+        std::vector<int64_t> off(batch->n_modules + 1);
+        if (cudaMemcpyAsync(off.data(), batch->mod_off, 8 * off.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return SPV_E_CUDA;
+        P.persistent = 0;
+        rc = 0;
+        for (int m = 0; m < batch->n_modules && !rc; m++) {
+            long long len = off[m + 1] - off[m];
+            long long nt = len > 0 ? (len + c.T - 1) / c.T : 1;
+            rc = dispatch_tile(P, c, (int)nt, st);
+        }
+    }
+    if (rc) return rc;
+    int nb = (batch->n_modules + 255) / 256;
+    SPV_LAUNCH("k_finalize", st, k_finalize<<<nb, 256, 0, st>>>(P));
+    if (validate) SPV_LAUNCH("k_fixup", st, k_fixup<<<64, FIX_NT, 0, st>>>(P));
+    return cudaPeekAtLastError() == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;
+}
+
+extern "C" int spv_decode_batch(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row,
+                                void *workspace, size_t workspace_bytes, const spv_config *cfg, spv_stream_t stream)
+{
+    return spv_process_batch(batch, table, status, err_row, 0, nullptr, 0, workspace, workspace_bytes, 0, cfg,
+                             stream);
+}
+
+extern "C" int spv_validate_batch(const spv_batch *batch, const spv_table *table, uint32_t *status,
+                                  int64_t *err_row, void *workspace, size_t workspace_bytes, int64_t arena_words,
+                                  spv_stream_t stream)
+{
+    Cfg c;
+    if (!check_batch(batch) || !table || !status || !err_row || resolve_cfg(nullptr, &c)) return SPV_E_ARG;
+    if (!table->op || !table->wc || !table->off || !table->rid || !table->mod || !table->mod_first_row ||
+        !table->mod_n_instr)
+        return SPV_E_ARG;
+    Layout L = make_layout(batch->n_modules, batch->n_words, arena_words, c.T);
+    if (!workspace || workspace_bytes < L.total) return SPV_E_WORKSPACE;
+    if (batch->n_modules == 0) return SPV_SUCCESS;
+    cudaStream_t st = (cudaStream_t)stream;
+    Params P = base_params(batch, workspace, L);
+    P.op = table->op; P.wc = table->wc; P.off = table->off; P.rtype = table->rtype; P.rid = table->rid;
+    P.mod = table->mod; P.first_row = table->mod_first_row; P.n_instr = table->mod_n_instr;
+    P.cap_rows = table->capacity_rows;
+    P.status = status; P.err_row = err_row;
+    P.validate = 1;
+    P.table_mode = 1;
+    P.max_spins = c.max_spins;
+    P.stall_tile = -1;
+    int nsm = sm_count();
+    int nb = (batch->n_modules + 255) / 256;
+    SPV_LAUNCH("k_prepass", st, k_prepass<<<1, 1024, 0, st>>>(P, c.T));
+    SPV_LAUNCH("k_tiles", st, k_tiles<<<nsm * 4, 256, 0, st>>>(P));
+    SPV_LAUNCH("k_table_framing", st, k_table_framing<<<nb, 256, 0, st>>>(P));
+    SPV_LAUNCH("k_validate_rows", st, k_validate_rows<<<nsm * 8, 256, 0, st>>>(P));
+    SPV_LAUNCH("k_finalize", st, k_finalize<<<nb, 256, 0, st>>>(P));
+    SPV_LAUNCH("k_fixup", st, k_fixup<<<64, FIX_NT, 0, st>>>(P));
+    return cudaPeekAtLastError() == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;
+}
+
+extern "C" int spv_encode_batch(const spv_batch *src, const spv_table *table, uint32_t *out_words,
+                                int recompute_bound, spv_stream_t stream)
+{
+    if (!check_batch(src) || !table || !out_words || !table->mod_first_row || !table->op || !table->wc ||
+        !table->off || !table->rtype || !table->rid || !table->mod)
+        return SPV_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (src->n_words &&
+        cudaMemcpyAsync(out_words, src->words, 4 * (size_t)src->n_words, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return SPV_E_CUDA;
+    if (src->n_modules == 0) return SPV_SUCCESS;
+    if (recompute_bound)
+        SPV_LAUNCH("k_encode_bound_init", st, k_encode_bound_init<<<(src->n_modules + 255) / 256, 256, 0, st>>>(src->words, src->mod_off, src->n_modules,
+                                                                          out_words));
+    int nsm = sm_count();
+    SPV_LAUNCH("k_encode_rows", st, k_encode_rows<<<nsm * 8, 256, 0, st>>>(src->words, src->mod_off, table->op, table->wc, table->off,
+                                           table->rtype, table->rid, table->mod, table->mod_first_row,
+                                           src->n_modules, table->capacity_rows, out_words, recompute_bound));
+    return cudaPeekAtLastError() == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;
+}

@@ -1,0 +1,333 @@
+"""Python binding of the C ABI in include/spv.h (libspvgpu.so).
+
+Argument marshalling only: every step of decode / validate / encode /
+disassemble runs in the library's CUDA kernels. PyTorch provides device
+memory (tensors) and streams. There is no CPU fallback: if the library is
+missing or cannot be loaded, every call raises.
+
+Two layers:
+  * ``spv_*`` functions with the C names and raw pointer arguments;
+  * ``process`` / ``decode`` / ``validate`` / ``encode`` / ``disassemble``,
+    which take torch tensors, allocate outputs and workspace with torch and
+    return tensors (uint32 / uint16 data are held in int32 / int16 tensors).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspvgpu.so")
+
+STATUS = [
+    "OK", "BAD_MAGIC", "BAD_HEADER", "TRUNCATED", "ZERO_WORDCOUNT", "UNKNOWN_OPCODE", "BAD_OPERANDS",
+    "ID_OUT_OF_BOUND", "DUP_RESULT_ID", "NO_CAPABILITY", "NO_MEMORY_MODEL", "MULTI_MEMORY_MODEL",
+    "NO_ENTRY_POINT", "NO_FUNCTION", "MISSING_CAPABILITY", "TIMEOUT", "CAPACITY",
+]
+SPV_SUCCESS, SPV_E_ARG, SPV_E_WORKSPACE, SPV_E_CUDA, SPV_E_UNSUPPORTED = 0, -1, -2, -3, -4
+
+P = ctypes.c_void_p
+
+
+class SpvBatch(ctypes.Structure):
+    _fields_ = [("words", P), ("mod_off", P), ("n_modules", ctypes.c_int32), ("n_words", ctypes.c_int64)]
+
+
+class SpvTable(ctypes.Structure):
+    _fields_ = [("op", P), ("wc", P), ("off", P), ("rtype", P), ("rid", P), ("mod", P),
+                ("mod_first_row", P), ("mod_n_instr", P), ("capacity_rows", ctypes.c_int64)]
+
+
+class SpvConfig(ctypes.Structure):
+    _fields_ = [("tile_words", ctypes.c_int32), ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("per_module", ctypes.c_int32), ("max_spins", ctypes.c_int64), ("test_stall_tile", ctypes.c_int64)]
+
+
+class SpvDisOpts(ctypes.Structure):
+    _fields_ = [("inline_names", ctypes.c_int32), ("header", ctypes.c_int32)]
+
+
+class SpvError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def load():
+    """Load libspvgpu.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libspvgpu.so not built ({LIB_PATH}); run paper_2305_09493_b300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    BP, TP, CP, DOP = (ctypes.POINTER(SpvBatch), ctypes.POINTER(SpvTable), ctypes.POINTER(SpvConfig),
+                       ctypes.POINTER(SpvDisOpts))
+    i32, i64, sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    lib.spv_workspace_bytes.restype = sz
+    lib.spv_workspace_bytes.argtypes = [i32, i64, i64, CP]
+    lib.spv_process_batch.restype = ctypes.c_int
+    lib.spv_process_batch.argtypes = [BP, TP, P, P, ctypes.c_int, P, ctypes.c_int, P, sz, i64, CP, P]
+    lib.spv_decode_batch.restype = ctypes.c_int
+    lib.spv_decode_batch.argtypes = [BP, TP, P, P, P, sz, CP, P]
+    lib.spv_validate_batch.restype = ctypes.c_int
+    lib.spv_validate_batch.argtypes = [BP, TP, P, P, P, sz, i64, P]
+    lib.spv_encode_batch.restype = ctypes.c_int
+    lib.spv_encode_batch.argtypes = [BP, TP, P, ctypes.c_int, P]
+    lib.spv_dis_workspace_bytes.restype = sz
+    lib.spv_dis_workspace_bytes.argtypes = [i32, i64, i64, i64]
+    lib.spv_disassemble_batch.restype = ctypes.c_int
+    lib.spv_disassemble_batch.argtypes = [BP, TP, DOP, P, ctypes.c_uint64, P, P, P, sz, i64, P]
+    lib.spv_op_info.restype = ctypes.c_int
+    lib.spv_op_info.argtypes = [ctypes.c_uint32, P, P, P, P]
+    lib.spv_enum_info.restype = ctypes.c_int
+    lib.spv_enum_info.argtypes = [ctypes.c_char_p, ctypes.c_uint32, P, P]
+    lib.spv_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------------
+# raw C-named layer
+# ---------------------------------------------------------------------------
+def spv_workspace_bytes(n_modules, n_words, arena_words=0, cfg=None):
+    return load().spv_workspace_bytes(n_modules, n_words, arena_words, ctypes.byref(cfg) if cfg else None)
+
+
+def spv_dis_workspace_bytes(n_modules, n_words, n_rows_capacity, arena_words=0):
+    return load().spv_dis_workspace_bytes(n_modules, n_words, n_rows_capacity, arena_words)
+
+
+def spv_process_batch(batch, table, status, err_row, validate, out_words, recompute_bound, workspace, ws_bytes,
+                      arena_words, cfg, stream):
+    return load().spv_process_batch(ctypes.byref(batch), ctypes.byref(table), status, err_row, validate,
+                                    out_words, recompute_bound, workspace, ws_bytes, arena_words,
+                                    ctypes.byref(cfg) if cfg else None, stream)
+
+
+def spv_decode_batch(batch, table, status, err_row, workspace, ws_bytes, cfg, stream):
+    return load().spv_decode_batch(ctypes.byref(batch), ctypes.byref(table), status, err_row, workspace,
+                                   ws_bytes, ctypes.byref(cfg) if cfg else None, stream)
+
+
+def spv_validate_batch(batch, table, status, err_row, workspace, ws_bytes, arena_words, stream):
+    return load().spv_validate_batch(ctypes.byref(batch), ctypes.byref(table), status, err_row, workspace,
+                                     ws_bytes, arena_words, stream)
+
+
+def spv_encode_batch(batch, table, out_words, recompute_bound, stream):
+    return load().spv_encode_batch(ctypes.byref(batch), ctypes.byref(table), out_words, recompute_bound, stream)
+
+
+def spv_disassemble_batch(batch, table, opts, text, text_capacity, text_off, dis_status, workspace, ws_bytes,
+                          arena_words, stream):
+    return load().spv_disassemble_batch(ctypes.byref(batch), ctypes.byref(table), ctypes.byref(opts), text,
+                                        text_capacity, text_off, dis_status, workspace, ws_bytes, arena_words,
+                                        stream)
+
+
+def spv_op_info(op):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    name = ctypes.c_char_p()
+    if load().spv_op_info(op, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(name)):
+        return None
+    return name.value.decode(), a.value, b.value, c.value
+
+
+def spv_enum_info(kind, value):
+    name = ctypes.c_char_p()
+    cap = ctypes.c_int()
+    if load().spv_enum_info(kind.encode(), value, ctypes.byref(name), ctypes.byref(cap)):
+        return None
+    return name.value.decode(), cap.value
+
+
+def spv_version():
+    return load().spv_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# torch layer
+# ---------------------------------------------------------------------------
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(rc, what):
+    if rc != SPV_SUCCESS:
+        raise SpvError(f"{what} failed with code {rc}")
+
+
+def make_config(tile_words=0, threads=0, ctas_per_sm=0, per_module=0, max_spins=0, test_stall_tile=0):
+    return SpvConfig(tile_words, threads, ctas_per_sm, per_module, max_spins, test_stall_tile)
+
+
+class Table:
+    """Device columns of the structure-of-arrays instruction table."""
+
+    def __init__(self, n_modules, capacity_rows, device):
+        e = lambda n, dt: torch.empty(max(1, n), dtype=dt, device=device)
+        self.op = e(capacity_rows, torch.int16)
+        self.wc = e(capacity_rows, torch.int16)
+        self.off = e(capacity_rows, torch.int64)
+        self.rtype = e(capacity_rows, torch.int32)
+        self.rid = e(capacity_rows, torch.int32)
+        self.mod = e(capacity_rows, torch.int32)
+        self.mod_first_row = e(n_modules + 1, torch.int64)
+        self.mod_n_instr = e(n_modules, torch.int32)
+        self.capacity_rows = capacity_rows
+
+    def c(self):
+        return SpvTable(self.op.data_ptr(), self.wc.data_ptr(), self.off.data_ptr(), self.rtype.data_ptr(),
+                        self.rid.data_ptr(), self.mod.data_ptr(), self.mod_first_row.data_ptr(),
+                        self.mod_n_instr.data_ptr(), self.capacity_rows)
+
+    def to_numpy(self, n_rows=None):
+        """Host copy with the table's own unsigned dtypes."""
+        import numpy as np
+        if n_rows is None:
+            n_rows = int(self.mod_first_row[-1].item())
+        n = min(n_rows, self.capacity_rows)
+        cpu = lambda t, k: t[:k].cpu().numpy()
+        return {
+            "op": cpu(self.op, n).view(np.uint16), "wc": cpu(self.wc, n).view(np.uint16),
+            "off": cpu(self.off, n).view(np.uint64), "rtype": cpu(self.rtype, n).view(np.uint32),
+            "rid": cpu(self.rid, n).view(np.uint32), "mod": cpu(self.mod, n).view(np.uint32),
+            "first_row": self.mod_first_row.cpu().numpy(), "n_instr": self.mod_n_instr.cpu().numpy().view(np.uint32),
+        }
+
+
+def batch_of(words, mod_off):
+    return SpvBatch(words.data_ptr(), mod_off.data_ptr(), mod_off.numel() - 1, words.numel())
+
+
+class Workspace:
+    """Caller-owned workspace reused across calls of the same batch shape."""
+
+    def __init__(self, n_modules, n_words, device, arena_words=0, cfg=None):
+        self.bytes = spv_workspace_bytes(n_modules, n_words, arena_words, cfg)
+        if self.bytes == 0 and (n_modules or n_words):
+            raise SpvError("invalid configuration for workspace")
+        self.buf = torch.empty(max(1, self.bytes), dtype=torch.uint8, device=device)
+        self.arena_words = arena_words
+
+
+def process(words, mod_off, *, validate=True, encode=False, recompute_bound=True, cfg=None, table=None,
+            workspace=None, out=None, stream=None, capacity_rows=None, arena_words=0):
+    """Decode (+ validate) (+ encode) a batch on its device in one persistent
+    launch. words: int32 device tensor (the uint32 words); mod_off: int64
+    device tensor of n_modules + 1 offsets. Returns a dict of tensors."""
+    m = mod_off.numel() - 1
+    dev = words.device
+    cap = capacity_rows if capacity_rows is not None else max(1, words.numel())
+    if table is None:
+        table = Table(m, cap, dev)
+    if workspace is None:
+        workspace = Workspace(m, words.numel(), dev, arena_words, cfg)
+    status = torch.empty(max(1, m), dtype=torch.int32, device=dev)
+    err_row = torch.empty(max(1, m), dtype=torch.int64, device=dev)
+    if encode and out is None:
+        out = torch.empty_like(words)
+    b, t = batch_of(words, mod_off), table.c()
+    rc = spv_process_batch(b, t, _ptr(status), _ptr(err_row), 1 if validate else 0, _ptr(out) if encode else None,
+                           1 if recompute_bound else 0, _ptr(workspace.buf), workspace.bytes,
+                           workspace.arena_words, cfg, _stream(stream))
+    _check(rc, "spv_process_batch")
+    return {"table": table, "status": status[:m], "err_row": err_row[:m], "out": out if encode else None,
+            "workspace": workspace}
+
+
+def decode(words, mod_off, **kw):
+    return process(words, mod_off, validate=False, encode=False, **kw)
+
+
+def validate(words, mod_off, table, *, workspace=None, stream=None, arena_words=0):
+    """Validate from an existing decoded table."""
+    m = mod_off.numel() - 1
+    dev = words.device
+    if workspace is None:
+        workspace = Workspace(m, words.numel(), dev, arena_words)
+    status = torch.empty(max(1, m), dtype=torch.int32, device=dev)
+    err_row = torch.empty(max(1, m), dtype=torch.int64, device=dev)
+    rc = spv_validate_batch(batch_of(words, mod_off), table.c(), _ptr(status), _ptr(err_row), _ptr(workspace.buf),
+                            workspace.bytes, workspace.arena_words, _stream(stream))
+    _check(rc, "spv_validate_batch")
+    return status[:m], err_row[:m]
+
+
+def encode(words, mod_off, table, *, recompute_bound=True, out=None, stream=None):
+    """Re-encode from a (possibly edited) table."""
+    if out is None:
+        out = torch.empty_like(words)
+    rc = spv_encode_batch(batch_of(words, mod_off), table.c(), _ptr(out), 1 if recompute_bound else 0,
+                          _stream(stream))
+    _check(rc, "spv_encode_batch")
+    return out
+
+
+class DisWorkspace:
+    def __init__(self, n_modules, n_words, capacity_rows, device, arena_words=0):
+        self.bytes = spv_dis_workspace_bytes(n_modules, n_words, capacity_rows, arena_words)
+        self.buf = torch.empty(max(1, self.bytes), dtype=torch.uint8, device=device)
+        self.arena_words = arena_words
+
+
+def disassemble(words, mod_off, table, *, inline_names=True, header=True, text=None, workspace=None, stream=None,
+                arena_words=0, sync=True):
+    """Text of every module. With sync (default) the call waits for the
+    stream, grows the text buffer if needed, and returns
+    (text uint8 tensor trimmed to its size, text_off int64 tensor, dis_status)."""
+    m = mod_off.numel() - 1
+    dev = words.device
+    if workspace is None:
+        workspace = DisWorkspace(m, words.numel(), table.capacity_rows, dev, arena_words)
+    text_off = torch.empty(m + 1, dtype=torch.int64, device=dev)
+    dis_status = torch.empty(max(1, m), dtype=torch.int32, device=dev)
+    if text is None:
+        text = torch.empty(max(1, 8 * words.numel()), dtype=torch.uint8, device=dev)
+    opts = SpvDisOpts(1 if inline_names else 0, 1 if header else 0)
+    for _ in range(2):
+        rc = spv_disassemble_batch(batch_of(words, mod_off), table.c(), opts, _ptr(text), text.numel(),
+                                   _ptr(text_off), _ptr(dis_status), _ptr(workspace.buf), workspace.bytes,
+                                   workspace.arena_words, _stream(stream))
+        _check(rc, "spv_disassemble_batch")
+        if not sync:
+            return text, text_off, dis_status[:m]
+        total = int(text_off[-1].item())
+        if total <= text.numel():
+            return text[:total], text_off, dis_status[:m]
+        text = torch.empty(total, dtype=torch.uint8, device=dev)
+    raise SpvError("text buffer sizing failed")
+
+
+# ---------------------------------------------------------------------------
+# per-kernel timing of the library's launches
+# ---------------------------------------------------------------------------
+def profile_enable(on=True):
+    lib = load()
+    lib.spv_profile_enable.restype = ctypes.c_int
+    lib.spv_profile_enable.argtypes = [ctypes.c_int]
+    return lib.spv_profile_enable(1 if on else 0)
+
+
+def profile_read(max_kernels=64):
+    """{kernel name: (launches, total ms)} of the launches recorded since
+    profile_enable(True)."""
+    lib = load()
+    lib.spv_profile_read.restype = ctypes.c_int
+    lib.spv_profile_read.argtypes = [ctypes.c_int, P, P, P]
+    names = (ctypes.c_char_p * max_kernels)()
+    launches = (ctypes.c_int64 * max_kernels)()
+    ms = (ctypes.c_double * max_kernels)()
+    n = lib.spv_profile_read(max_kernels, names, launches, ms)
+    if n < 0:
+        raise SpvError(f"spv_profile_read failed with code {n}")
+    return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(n, max_kernels))}

@@ -1,0 +1,340 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer and string work: every comparison is exact (tables, statuses, error
+rows, encoded words, disassembly bytes)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_09493_b300 import synth
+from tests import spvhand as H
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    from paper_2305_09493_b300 import build, spvgpu
+    build.build()
+    spvgpu.load()
+    return spvgpu
+
+
+def dev(words, mod_off):
+    w = torch.from_numpy(np.ascontiguousarray(words, np.uint32).view(np.int32)).cuda()
+    o = torch.from_numpy(np.ascontiguousarray(mod_off, np.int64)).cuda()
+    return w, o
+
+
+def run(gpu, words, mod_off, cfg=None, validate=True, encode=True, **kw):
+    w, o = dev(words, mod_off)
+    r = gpu.process(w, o, validate=validate, encode=encode, cfg=cfg, **kw)
+    torch.cuda.synchronize()
+    m = len(mod_off) - 1
+    out = {
+        "table": r["table"].to_numpy(),
+        "status": r["status"].cpu().numpy().view(np.uint32)[:m],
+        "err_row": r["err_row"].cpu().numpy()[:m],
+        "out": r["out"].cpu().numpy().view(np.uint32) if encode else None,
+        "_r": r, "_w": w, "_o": o,
+    }
+    return out
+
+
+def assert_table_equal(t, d, m):
+    n = d["n_rows"]
+    assert int(t["first_row"][m]) == n
+    for k in ("op", "wc", "off", "rtype", "rid", "mod"):
+        assert np.array_equal(t[k][:n], d[k]), k
+    assert np.array_equal(t["first_row"][:m], d["first_row"])
+    assert np.array_equal(t["n_instr"][:m], d["n_instr"])
+
+
+def check(gpu, words, mod_off, cfg=None, dis=False):
+    m = len(mod_off) - 1
+    g = run(gpu, words, mod_off, cfg)
+    d = oracle.decode(words, mod_off)
+    assert_table_equal(g["table"], d, m)
+    st, er = oracle.validate(words, mod_off)
+    bad = np.nonzero((g["status"] != st) | (g["err_row"] != er))[0]
+    assert len(bad) == 0, [(int(i), oracle.STATUS[st[i]], int(er[i]), gpu.STATUS[g["status"][i]], int(g["err_row"][i]))
+                           for i in bad[:10]]
+    assert np.array_equal(g["out"], oracle.encode(words, mod_off, d, True))
+    # decode-only statuses (header / framing)
+    g2 = run(gpu, words, mod_off, cfg, validate=False, encode=False)
+    assert np.array_equal(g2["status"], d["status"])
+    assert np.array_equal(g2["err_row"], d["err_row"])
+    if dis:
+        check_dis(gpu, words, mod_off, g)
+    return g
+
+
+def check_dis(gpu, words, mod_off, g, modes=((True, True), (False, False), (True, False))):
+    for inline, header in modes:
+        text, toff, dst = gpu.disassemble(g["_w"], g["_o"], g["_r"]["table"], inline_names=inline, header=header)
+        torch.cuda.synchronize()
+        want, woff = oracle.disassemble(words, mod_off, inline, header)
+        got = text.cpu().numpy().tobytes()
+        if got != want:
+            i = next(k for k in range(min(len(got), len(want))) if got[k] != want[k]) if got[:len(want)] != want[:len(got)] else min(len(got), len(want))
+            raise AssertionError(f"text differs at byte {i}: got {got[max(0,i-80):i+80]!r} want {want[max(0,i-80):i+80]!r}")
+        assert np.array_equal(toff.cpu().numpy(), woff)
+
+
+# ---------------------------------------------------------------------------
+def test_single_modules(gpu):
+    for seed in range(4):
+        w, off, _, _ = synth.single_module(seed)
+        check(gpu, w, off, dis=True)
+
+
+def test_small_batch_ragged(gpu):
+    n_instr, n_k = synth.batch_shape(300, 11, median=1500, lo=200, hi=20000)
+    w, off = synth.batch(n_instr, n_k, 11)
+    check(gpu, w, off, dis=True)
+
+
+@pytest.mark.parametrize("tile,threads", [(4096, 256), (2048, 256), (2048, 128), (1024, 128)])
+def test_tile_configs(gpu, tile, threads):
+    n_instr, n_k = synth.batch_shape(60, 3, median=3000, lo=200, hi=30000)
+    w1, off1 = synth.batch(n_instr, n_k, 3)
+    w2, off2, _, _ = synth.large_module(9, n_instr=150_000, n_funcs=20)
+    words = np.concatenate([w1, w2])
+    offs = np.concatenate([off1, off1[-1] + off2[1:]])
+    check(gpu, words, offs, cfg=gpu.make_config(tile_words=tile, threads=threads), dis=(tile == 2048 and threads == 128))
+
+
+def test_per_module_path_matches(gpu):
+    n_instr, n_k = synth.batch_shape(40, 5, median=2000, lo=200, hi=20000)
+    w, off = synth.batch(n_instr, n_k, 5)
+    a = check(gpu, w, off, cfg=gpu.make_config(per_module=1))
+    b = run(gpu, w, off)
+    assert np.array_equal(a["status"], b["status"]) and np.array_equal(a["out"], b["out"])
+
+
+def test_large_module_with_strings(gpu):
+    w, off, starts, bound = synth.large_module(2, n_instr=400_000, n_funcs=50)
+    g = check(gpu, w, off, dis=True)
+    assert np.array_equal(g["table"]["off"].astype(np.int64), starts)
+
+
+# ---------------------------------------------------------------------------
+# edge cases and corruptions
+# ---------------------------------------------------------------------------
+def hand_modules():
+    base = H.minimal_body()
+    mods = [H.module(base, bound=8), H.module(base, bound=0), H.module([], bound=1)]
+    good = H.module(base, bound=8)
+    for n in range(0, 6):
+        mods.append(good[:n])
+    mods.append(good[:-3])
+    for i, v in [(0, 0x03022307), (1, 0x00020000), (4, 1), (1, 0x00010700)]:
+        x = good.copy(); x[i] = v; mods.append(x)
+    b = list(base); b[0] = H.ins(H.OpCapability, H.CAP_KERNEL); mods.append(H.module(b, bound=8))
+    b = list(base); b.insert(11, H.ins(H.OpIAdd, 2, 7, 4, 4)); b.insert(12, H.ins(H.OpIAdd, 2, 7, 4, 4)); mods.append(H.module(b, bound=8))
+    b = list(base); b.insert(4, [(1 << 16) | 9999]); mods.append(H.module(b, bound=8))
+    b = list(base); b[3] = [(4 << 16) | H.OpEntryPoint, H.EXEC_KERNEL, 5, 0x6b6b6b6b]; mods.append(H.module(b, bound=8))
+    b = list(base); b[10] = H.ins(H.OpIAdd, 2, 7, 4, 99); mods.append(H.module(b, bound=8))
+    mods.append(H.module(base[:2] + base[3:], bound=8))
+    mods.append(H.module(base[:3] + [base[2]] + base[3:], bound=8))
+    mods.append(H.module(base[:3] + base[4:], bound=8))
+    mods.append(H.module([i for i in base if i[0] & 0xffff != H.OpFunction], bound=8))
+    mods.append(H.module([H.ins(H.OpTypeVoid, 1)], bound=8))
+    b = list(base); b.insert(6, H.ins(H.OpTypeInt, 8, 64, 0)); mods.append(H.module(b, bound=9))
+    b = list(base); b[0] = H.ins(H.OpCapability, H.CAP_GENERIC_POINTER); mods.append(H.module(b, bound=8))
+    return mods
+
+
+def test_edge_and_hand_built_modules(gpu):
+    mods = hand_modules()
+    w, off = H.batch(mods)
+    check(gpu, w, off, dis=True)
+    # the same modules as single-module batches, and an empty module between others
+    for mm in mods[:8]:
+        ww, oo = H.batch([mm])
+        check(gpu, ww, oo)
+    ww, oo = H.batch([mods[0], mods[0][:0], mods[0]])
+    check(gpu, ww, oo, dis=True)
+
+
+def test_empty_batch(gpu):
+    w = torch.zeros(1, dtype=torch.int32, device="cuda")[:0]
+    o = torch.zeros(1, dtype=torch.int64, device="cuda")
+    r = gpu.process(w, o)
+    torch.cuda.synchronize()
+    assert r["status"].numel() == 0
+
+
+def test_single_word_corruptions(gpu):
+    base = H.module(H.minimal_body(), bound=8)
+    values = [0, 1, 0xFFFFFFFF, 0x00010000, 0x00020000, 0x00050080, 0x7FFF0011, 0x00030011, 7, 8, 9999]
+    mods = []
+    for i in range(len(base)):
+        for v in values:
+            x = base.copy(); x[i] = v; mods.append(x)
+    w, off = H.batch(mods)
+    check(gpu, w, off, dis=True)
+
+
+def corrupt(words, starts, bound, rng, kind):
+    x = words.copy()
+    r = int(rng.integers(0, len(starts)))
+    p = int(starts[r])
+    wc = int(x[p] >> 16)
+    if kind == "opcode":
+        x[p] = (x[p] & 0xFFFF0000) | int(rng.integers(256, 65536))
+    elif kind == "wc":
+        x[p] = (x[p] & 0xFFFF) | (int(rng.integers(0, 6)) << 16)
+    elif kind == "operand" and wc > 1:
+        x[p + int(rng.integers(1, wc))] = int(rng.choice([0, bound, bound + 7, 0xFFFFFFFF, int(rng.integers(1, bound))]))
+    elif kind == "dup":
+        q = int(starts[int(rng.integers(0, len(starts)))])
+        if wc >= 3 and (x[q] >> 16) >= 3:
+            x[p + 2] = x[q + 2]
+    elif kind == "random":
+        x[int(rng.integers(0, len(x)))] = int(rng.integers(0, 2**32))
+    elif kind == "header":
+        x[int(rng.integers(0, 5))] ^= 1 << int(rng.integers(0, 32))
+    elif kind == "truncate":
+        x = x[: int(rng.integers(5, len(x)))]
+    return x
+
+
+def test_random_corruptions(gpu):
+    rng = np.random.default_rng(1234)
+    mods = []
+    for seed in range(8):
+        w, off, starts, bound = synth.single_module(1000 + seed)
+        for kind in ("opcode", "wc", "operand", "dup", "random", "header", "truncate"):
+            for _ in range(6):
+                mods.append(corrupt(w, starts, bound, rng, kind))
+    words, offs = H.batch(mods)
+    g = check(gpu, words, offs, dis=True)
+    st = set(int(s) for s in g["status"])
+    assert len(st) >= 8, st
+
+
+def test_duplicates_across_chunks_and_missing_caps(gpu):
+    w, off, starts, bound = synth.large_module(4, n_instr=60_000, n_funcs=6, string_permille=0)
+    d = oracle.decode(w, off)
+    rows = np.nonzero(d["rid"] > 0)[0]
+    mods = []
+    for a, b in [(rows[10], rows[5000]), (rows[3000], rows[3001]), (rows[100], rows[40000]), (rows[-1], rows[-2])]:
+        x = w.copy()
+        pb = int(d["off"][b]); pa = int(d["off"][a])
+        x[pb + (2 if oracle.op_info(int(d["op"][b]))[1] else 1)] = x[pa + (2 if oracle.op_info(int(d["op"][a]))[1] else 1)]
+        mods.append(x)
+    x = w.copy()
+    caps = np.nonzero(d["op"] == 17)[0]
+    x[int(d["off"][caps[-1]]) + 1] = 39          # Int64 -> Int8: 64-bit int types now miss a capability
+    mods.append(x)
+    words, offs = H.batch(mods)
+    check(gpu, words, offs)
+
+
+# ---------------------------------------------------------------------------
+# table-level entry points
+# ---------------------------------------------------------------------------
+def test_validate_from_table_and_encode_edited(gpu):
+    n_instr, n_k = synth.batch_shape(50, 21, median=1500, lo=200, hi=10000)
+    w, off = synth.batch(n_instr, n_k, 21)
+    rng = np.random.default_rng(5)
+    mods = []
+    for m in range(50):
+        x = w[off[m]:off[m + 1]].copy()
+        if m % 3 == 0:
+            x[int(rng.integers(5, len(x)))] = int(rng.integers(0, 2**32))
+        mods.append(x)
+    words, offs = H.batch(mods)
+    g = run(gpu, words, offs)
+    st, er = gpu.validate(g["_w"], g["_o"], g["_r"]["table"])
+    torch.cuda.synchronize()
+    assert np.array_equal(st.cpu().numpy().view(np.uint32), g["status"])
+    assert np.array_equal(er.cpu().numpy(), g["err_row"])
+    # edit the table: rename result ids and swap opcodes, then encode
+    t = g["_r"]["table"]
+    d = oracle.decode(words, offs)
+    n = d["n_rows"]
+    sel = np.nonzero(d["rid"] > 0)[0][::7]
+    d["rid"][sel] += 1000
+    d["op"][sel[::2]] = np.where(d["op"][sel[::2]] == 128, 129, d["op"][sel[::2]])
+    t.rid[:n] = torch.from_numpy(d["rid"].view(np.int32)).cuda()
+    t.op[:n] = torch.from_numpy(d["op"].view(np.int16)).cuda()
+    out = gpu.encode(g["_w"], g["_o"], t, recompute_bound=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.encode(words, offs, d, True))
+    out2 = gpu.encode(g["_w"], g["_o"], t, recompute_bound=False)
+    torch.cuda.synchronize()
+    assert np.array_equal(out2.cpu().numpy().view(np.uint32), oracle.encode(words, offs, d, False))
+
+
+def test_row_capacity(gpu):
+    n_instr, n_k = synth.batch_shape(20, 8, median=1000, lo=200, hi=3000)
+    w, off = synth.batch(n_instr, n_k, 8)
+    d = oracle.decode(w, off)
+    cap = int(d["first_row"][10]) + 7
+    g = run(gpu, w, off, capacity_rows=cap)
+    st, er = oracle.validate(w, off)
+    full = [m for m in range(20) if d["first_row"][m] + d["n_instr"][m] <= cap]
+    assert full == list(range(10))
+    assert np.array_equal(g["status"][:10], st[:10])
+    assert all(gpu.STATUS[s] == "CAPACITY" for s in g["status"][10:])
+    for k in ("op", "wc", "off", "rid"):
+        assert np.array_equal(g["table"][k][:cap], d[k][:cap])
+
+
+def test_arena_capacity(gpu):
+    n_instr, n_k = synth.batch_shape(20, 9, median=1000, lo=200, hi=3000)
+    w, off = synth.batch(n_instr, n_k, 9)
+    bounds = [int(w[off[m] + 3]) for m in range(20)]
+    need = np.cumsum([(b + 31) // 32 for b in bounds])
+    g = run(gpu, w, off, arena_words=int(need[4]))
+    st, er = oracle.validate(w, off)
+    assert np.array_equal(g["status"][:5], st[:5])
+    assert all(gpu.STATUS[s] == "CAPACITY" for s in g["status"][5:])
+
+
+def test_text_capacity_reports_size(gpu):
+    w, off, _, _ = synth.single_module(3)
+    g = run(gpu, w, off)
+    text = torch.full((100,), 7, dtype=torch.uint8, device="cuda")
+    t, toff, _ = gpu.disassemble(g["_w"], g["_o"], g["_r"]["table"], text=text, sync=False)
+    torch.cuda.synchronize()
+    want, woff = oracle.disassemble(w, off, True, True)
+    assert int(toff[-1].item()) == len(want)
+    assert bool((text == 7).all())
+
+
+def test_bounded_wait_times_out_without_hanging(gpu):
+    w, off, _, _ = synth.large_module(6, n_instr=60_000, n_funcs=4)
+    cfg = gpu.make_config(tile_words=1024, threads=128, max_spins=2000, test_stall_tile=5)
+    g = run(gpu, w, off, cfg=cfg)
+    assert gpu.STATUS[g["status"][0]] == "TIMEOUT"
+    # the context is still usable and a normal call is exact
+    check(gpu, w, off)
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads
+# ---------------------------------------------------------------------------
+def test_full_size_batch_10k_modules(gpu):
+    w, off = synth.module_batch(10_000, 0)
+    g = run(gpu, w, off)
+    d = oracle.decode(w, off)
+    assert_table_equal(g["table"], d, 10_000)
+    st, er = oracle.validate(w, off)
+    assert np.array_equal(g["status"], st) and np.array_equal(g["err_row"], er)
+    assert np.array_equal(g["out"], oracle.encode(w, off, d, True))
+
+
+def test_full_size_large_module_and_text(gpu):
+    w, off, starts, bound = synth.large_module(0)
+    g = run(gpu, w, off)
+    d = oracle.decode(w, off)
+    assert_table_equal(g["table"], d, 1)
+    st, er = oracle.validate(w, off)
+    assert g["status"][0] == st[0] == 0
+    assert np.array_equal(g["out"], w)
+    check_dis(gpu, w, off, g, modes=((True, True),))
