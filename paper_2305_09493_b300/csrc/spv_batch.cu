@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(1024) k_prepass(Params P, int tile_words)
 }
 
 // per tile: owning module, cleared look-back states; clears the id arena
-__global__ void k_tiles(Params P)
+__global__ void k_tile_setup(Params P)
 {
     unsigned long long nt = P.ctrl->n_tiles;
     long long stride = (long long)gridDim.x * blockDim.x;
@@ -973,7 +973,7 @@ extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint3
     P.stall_tile = c.stall_tile;
     SPV_LAUNCH("k_prepass", st, k_prepass<<<1, 1024, 0, st>>>(P, c.T));
     int nsm = sm_count();
-    SPV_LAUNCH("k_tiles", st, k_tiles<<<nsm * 4, 256, 0, st>>>(P));
+    SPV_LAUNCH("k_tile_setup", st, k_tile_setup<<<nsm * 4, 256, 0, st>>>(P));
     if (cudaPeekAtLastError() != cudaSuccess) return SPV_E_CUDA;
     int rc;
     if (!c.per_module) {
@@ -1034,7 +1034,7 @@ extern "C" int spv_validate_batch(const spv_batch *batch, const spv_table *table
     int nsm = sm_count();
     int nb = (batch->n_modules + 255) / 256;
     SPV_LAUNCH("k_prepass", st, k_prepass<<<1, 1024, 0, st>>>(P, c.T));
-    SPV_LAUNCH("k_tiles", st, k_tiles<<<nsm * 4, 256, 0, st>>>(P));
+    SPV_LAUNCH("k_tile_setup", st, k_tile_setup<<<nsm * 4, 256, 0, st>>>(P));
     SPV_LAUNCH("k_table_framing", st, k_table_framing<<<nb, 256, 0, st>>>(P));
     SPV_LAUNCH("k_validate_rows", st, k_validate_rows<<<nsm * 8, 256, 0, st>>>(P));
     SPV_LAUNCH("k_finalize", st, k_finalize<<<nb, 256, 0, st>>>(P));
