@@ -147,6 +147,34 @@ int spv_process_batch(const spv_batch *batch, spv_table *table, uint32_t *status
                       void *workspace, size_t workspace_bytes, int64_t arena_words,
                       const spv_config *cfg, spv_stream_t stream);
 
+/* Size of the fixed device scratch used by spv_process_batch_noalloc. */
+#define SPV_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * spv_process_batch_noalloc -- spv_process_batch for callers that cannot
+ * allocate device memory (the paper has no counterpart; this is a library
+ * service). A host runtime that keeps all of a GPU's memory in its own pool,
+ * or a latency-bound serving loop where cudaMalloc could stall the device or
+ * fail under memory pressure, still passes its inputs and outputs but no
+ * workspace: the kernels' scratch is a fixed 32 MiB device array inside the
+ * library (SPV_NOALLOC_SCRATCH_BYTES), which every GPU that loads the
+ * library holds until the process exits. Nothing is allocated by the call.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - A batch whose workspace (spv_workspace_bytes with the default arena)
+ *     exceeds SPV_NOALLOC_SCRATCH_BYTES is rejected with SPV_E_WORKSPACE and
+ *     nothing is launched; cfg->per_module is rejected with
+ *     SPV_E_UNSUPPORTED.
+ *   - Every call on a device shares the array and leaves its contents behind;
+ *     each call clears on the device what it needs cleared. Two calls that
+ *     overlap on the GPU (different streams, no ordering) race on the array.
+ * Arguments and results are those of spv_process_batch.
+ */
+int spv_process_batch_noalloc(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row,
+                              int validate, uint32_t *out_words, int recompute_bound,
+                              const spv_config *cfg, spv_stream_t stream);
+
 /* spv_decode_batch -- spv_process_batch with validate = 0 and no encode. */
 int spv_decode_batch(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row,
                      void *workspace, size_t workspace_bytes, const spv_config *cfg, spv_stream_t stream);

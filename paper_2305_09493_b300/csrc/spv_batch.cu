@@ -27,6 +27,7 @@
 #include <string.h>
 #include <vector>
 #include <algorithm>
+#include <mutex>
 
 #include "../../include/spv.h"
 #include "spv_device.cuh"
@@ -1061,4 +1062,50 @@ extern "C" int spv_encode_batch(const spv_batch *src, const spv_table *table, ui
                                            table->rtype, table->rid, table->mod, table->mod_first_row,
                                            src->n_modules, table->capacity_rows, out_words, recompute_bound));
     return cudaPeekAtLastError() == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// spv_process_batch_noalloc: the fused decode / validate / encode without any
+// allocation by the caller or the library. Some callers cannot allocate
+// device memory: a host runtime that reserves all of a GPU's memory in its
+// own pool up front and forbids other allocations, or a latency-bound
+// serving loop where cudaMalloc could stall the device or fail under memory
+// pressure. They still own inputs and outputs; the scratch the kernels need
+// (tile look-back states, per-module aggregates, the result-id sets) lives
+// in the fixed array below instead of a caller-provided workspace.
+// ---------------------------------------------------------------------------
+namespace {
+// Every GPU that loads this library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SPV_NOALLOC_SCRATCH_BYTES];
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[1024];   // per device: the array's device address (host code cannot use its name)
+}  // namespace
+
+extern "C" int spv_process_batch_noalloc(const spv_batch *batch, spv_table *table, uint32_t *status,
+                                         int64_t *err_row, int validate, uint32_t *out_words,
+                                         int recompute_bound, const spv_config *cfg, spv_stream_t stream)
+{
+    Cfg c;
+    if (!check_batch(batch) || resolve_cfg(cfg, &c)) return SPV_E_ARG;
+    if (c.per_module) return SPV_E_UNSUPPORTED;
+    if (make_layout(batch->n_modules, batch->n_words, 0, c.T).total > (size_t)SPV_NOALLOC_SCRATCH_BYTES)
+        return SPV_E_WORKSPACE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 1024) return SPV_E_CUDA;
+    void *scratch = nullptr;
+    {
+        // set-up, once per device, with that device current
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SPV_E_CUDA;
+            g_noalloc_addr[dev] = p;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    // the kernels initialise every part of the scratch they read (look-back
+    // states, counters, module states and id sets are cleared on the device
+    // at the start of each call), so the previous call's contents never leak
+    return spv_process_batch(batch, table, status, err_row, validate, out_words, recompute_bound, scratch,
+                             (size_t)SPV_NOALLOC_SCRATCH_BYTES, 0, cfg, stream);
 }

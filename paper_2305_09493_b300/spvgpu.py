@@ -86,6 +86,8 @@ def load():
     lib.spv_enum_info.restype = ctypes.c_int
     lib.spv_enum_info.argtypes = [ctypes.c_char_p, ctypes.c_uint32, P, P]
     lib.spv_version.restype = ctypes.c_char_p
+    lib.spv_process_batch_noalloc.restype = ctypes.c_int
+    lib.spv_process_batch_noalloc.argtypes = [BP, TP, P, P, ctypes.c_int, P, ctypes.c_int, CP, P]
     _lib = lib
     return lib
 
@@ -106,6 +108,17 @@ def spv_process_batch(batch, table, status, err_row, validate, out_words, recomp
     return load().spv_process_batch(ctypes.byref(batch), ctypes.byref(table), status, err_row, validate,
                                     out_words, recompute_bound, workspace, ws_bytes, arena_words,
                                     ctypes.byref(cfg) if cfg else None, stream)
+
+
+def spv_process_batch_noalloc(batch, table, status, err_row, validate, out_words, recompute_bound, cfg, stream):
+    """spv_process_batch without a workspace: the library's fixed device
+    scratch (SPV_NOALLOC_SCRATCH_BYTES) is used instead, for callers that
+    cannot allocate device memory."""
+    return load().spv_process_batch_noalloc(ctypes.byref(batch), ctypes.byref(table), status, err_row, validate,
+                                            out_words, recompute_bound, ctypes.byref(cfg) if cfg else None, stream)
+
+
+SPV_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 def spv_decode_batch(batch, table, status, err_row, workspace, ws_bytes, cfg, stream):
