@@ -130,9 +130,9 @@ class Clocks:
 def algorithmic_bytes(kernel, W, N, L, M):
     return {
         "k_tile": 4 * W + 4 * W + 24 * N,                # words in; encoded words + 24-byte rows out
-        "k_dis_write_rows": 4 * W + 24 * N + L,          # words + op/wc/off/mod + row positions in; text out
-        "k_dis_len": 4 * W + 16 * N + 8 * N,             # words + op/wc/off/mod in; row positions out
+        "k_dis_main": 4 * W + 16 * N + L,                # words + op/wc/off/mod in; text out
         "k_dis_ids": 20 * N,                             # op/wc/off/mod/rid columns
+        "k_dis_namelen": 4 * N,                          # op column (OpName rows are few)
         "k_dis_clear": 0, "k_tile_setup": 0, "k_prepass": 40 * M, "k_finalize": 64 * M,
     }.get(kernel, 0)
 

@@ -217,13 +217,14 @@ typedef struct spv_dis_opts {
 size_t spv_dis_workspace_bytes(int32_t n_modules, int64_t n_words, int64_t n_rows_capacity, int64_t arena_words);
 
 /*
- * spv_disassemble_batch -- text of every module (section 3.4.4), two passes:
- * per-instruction length, exclusive scan into 64-bit offsets, write.
- * Module m's text is text[text_off[m] .. text_off[m+1]); text_off has
- * n_modules + 1 entries (device). If the total exceeds text_capacity nothing
- * is written but text_off is still filled: the caller compares
- * text_off[n_modules] with the capacity after the stream completes and calls
- * again with a larger buffer. A module with a header error has no text; a
+ * spv_disassemble_batch -- text of every module (section 3.4.4): every
+ * line is measured, the lengths are scanned into 64-bit offsets, and every
+ * line is written once. Module m's text is text[text_off[m] .. text_off[m+1]);
+ * text_off has n_modules + 1 entries (device). No byte at or past
+ * text_capacity is ever written; when text_off[n_modules] exceeds the
+ * capacity the text is incomplete and the caller calls again with a buffer of
+ * text_off[n_modules] bytes (text_off is always filled). A module with a
+ * header error has no text; a
  * module whose id tables do not fit the arena gets status SPV_CAPACITY in
  * dis_status (device, n_modules entries, may be NULL) and no text.
  * The text form: optional "; SPIR-V", "; Version: M.m",

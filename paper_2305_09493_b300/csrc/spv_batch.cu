@@ -474,13 +474,18 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
         const uint32_t bound = P.ms[m].bound;
         const long long arena_off = P.validate ? P.ms[m].arena_off : -1;
         const uint32_t id_slots = P.ms[m].id_slots;
-        for (unsigned r = tid; r < tile_count; r += NT) {
+        for (unsigned rb = 0; rb < tile_count; rb += NT) {
+            const unsigned r = rb + tid;
+            const bool valid = r < tile_count;
+            uint32_t ri = 0;
+            uint64_t req = 0;
+            if (valid) {
             uint32_t p = S16[r];
             uint32_t w0 = word(p);
             uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
             const spvt::OpDesc &d = TB.ops[op < 256 ? op : 0];
             bool known = op < 256 && (d.flags & 1);
-            uint32_t rt = 0, ri = 0;
+            uint32_t rt = 0;
             if (known) {
                 uint32_t q = 1;
                 if (d.flags & 2) { if (q < wc) rt = word(p + q); q++; }
@@ -494,7 +499,6 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             } else {
                 atomicOr(&s.flags, MF_CAPACITY);
             }
-            if (ri > 0) atomicMax(&s.max_rid, ri);
             if (P.validate) {
                 if (op == 17) { atomicAdd(&s.n_cap, 1u); if (wc >= 2) { uint32_t c = word(p + 1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); } }
                 else if (op == 14) atomicAdd(&s.n_mm, 1u);
@@ -509,13 +513,19 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                     else {
                         if ((d.flags & 4) && arena_off >= 0 && idset_insert(P.arena + arena_off, id_slots, ri))
                             atomicOr(&s.flags, MF_DUP);
-                        uint64_t req = wk.req | width_caps(iw, op, wc);
-                        if (req) {
-                            if ((uint32_t)req) atomicOr(&s.req_lo, (uint32_t)req);
-                            if ((uint32_t)(req >> 32)) atomicOr(&s.req_hi, (uint32_t)(req >> 32));
-                        }
+                        req = wk.req | width_caps(iw, op, wc);
                     }
                 }
+            }
+            }
+            // warp-level aggregation, then one shared atomic per warp
+            uint32_t mx = __reduce_max_sync(0xffffffffu, ri);
+            uint32_t rlo = __reduce_or_sync(0xffffffffu, (uint32_t)req);
+            uint32_t rhi = __reduce_or_sync(0xffffffffu, (uint32_t)(req >> 32));
+            if (lane == 0) {
+                if (mx) atomicMax(&s.max_rid, mx);
+                if (rlo) atomicOr(&s.req_lo, rlo);
+                if (rhi) atomicOr(&s.req_hi, rhi);
             }
         }
         // 5. encode. In the fused path every field an instruction writes back

@@ -186,6 +186,25 @@ __device__ Walk walk_instruction(const WordFn &word, uint32_t wc, const spvt::Op
 {
     const spvt::Tables &T = g_spv_tables;
     Walk r{true, false, 0};
+    if (d.fast & 1) {
+        // only fixed ids / literals and a plain tail: a length check and a
+        // range check of the id words (same result as the walk below)
+        const uint32_t need = 1u + d.nfixed, tail = d.fast >> 1;
+        r.ok = tail == 0 ? wc == need : (wc >= need && (tail != 3 || ((wc - need) & 1u) == 0));
+        if (r.ok) {
+            uint32_t mask = d.id_mask;
+            while (mask) {
+                int i = __ffs(mask) - 1;
+                mask &= mask - 1;
+                uint32_t v = word((uint32_t)i);
+                if (v == 0 || v >= bound) r.oob = true;
+            }
+            if (tail == 1 || tail == 3)
+                for (uint32_t i = need; i < wc; i++) { uint32_t v = word(i); if (v == 0 || v >= bound) r.oob = true; }
+        }
+        if (d.cap >= 0) r.req |= 1ull << d.cap;
+        return r;
+    }
     uint32_t pos = 1;
 #define SPV_ID_AT(p) do { uint32_t _v = word(p); if (_v == 0 || _v >= bound) r.oob = true; } while (0)
     if (d.flags & 2) { if (pos >= wc) { r.ok = false; return r; } SPV_ID_AT(pos); pos++; }

@@ -3,12 +3,21 @@
 // "inline names" and "header" options; one line per instruction as in
 // Listing 8).
 //
-// Two passes over the table's rows with one formatter, templated on its
-// output: pass 1 counts each row's bytes, scans the counts (block scan +
-// decoupled look-back) into 64-bit positions; pass 2 writes the bytes. Before
-// them, each module gets two id tables in a workspace arena: the row of the
-// first OpName naming each id (for inline names) and the row of the first
-// instruction defining each id (whether an OpConstant's type is a float).
+// The text of a batch is a sequence of items: for each module its header
+// lines (possibly empty), then one line per row of the module. Item i of
+// module m is its header when i == first_row[m] + m, else row
+// first_row[m] + (i - first_row[m] - m - 1). One persistent kernel takes
+// tiles of 512 items; per tile it
+//   1. measures every item (an arithmetic count of the formatter's output),
+//   2. scans the lengths in the block and gets the tile's 64-bit text base
+//      from a decoupled look-back over the predecessors' totals,
+//   3. formats every item once into shared memory and copies the tile's text
+//      out with 4-byte coalesced stores (tiles whose text exceeds the shared
+//      buffer format straight into global memory).
+// Before it, each module gets a per-id table in a workspace arena: the row
+// and name length of the first OpName naming the id (inline names) and the
+// row of the first instruction defining it (whether an OpConstant's type is
+// a float).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,9 +30,10 @@ using namespace spvd;
 namespace {
 
 constexpr uint32_t NOROW = 0xFFFFFFFFu;
-constexpr int DNT = 256;             // threads per CTA in the row passes
-constexpr int DPT = 8;               // rows per thread in the scan pass
-constexpr int DROWS = DNT * DPT;     // rows per scan tile
+constexpr int DNT = 256;                 // threads per CTA
+constexpr int IPT = 2;                   // items per thread
+constexpr int ITEMS = DNT * IPT;         // items per tile
+constexpr int TEXT_SMEM = 40 * 1024;     // shared text buffer per tile
 constexpr unsigned long long F_AGG = 1ull << 62, F_INC = 2ull << 62, F_MSK = 3ull << 62;
 
 struct DisCtrl {
@@ -31,16 +41,18 @@ struct DisCtrl {
     unsigned int timeout;
     unsigned long long arena_used;
     unsigned long long n_rows;
+    unsigned long long n_items;
 };
 
 struct DisMod {
-    uint32_t ok;             // header valid and tables fit
+    uint32_t ok;             // header valid and id table fits
     uint32_t bound;
-    long long arena_off;     // the module's id tables (see IdTab)
-    uint32_t slots;          // 0: direct tables indexed by id; else hash map of this many ids
-    uint32_t header_len;     // bytes of the header comment lines
+    long long arena_off;     // the module's id table
+    uint32_t slots;          // 0: direct table by id (3 words per id); else hash map (4 words per slot)
+    uint32_t header_len;     // bytes of the header comment lines (0 when not printed)
     uint32_t status;         // S_OK / header status / S_CAPACITY
-    unsigned long long hincl; // inclusive scan of header_len over modules
+    uint32_t pad;
+    long long item_base;     // index of the module's header item
 };
 
 struct DP {
@@ -48,89 +60,121 @@ struct DP {
     const int64_t *mod_off;
     int n_mod;
     const uint16_t *op; const uint16_t *wc; const uint64_t *off; const uint32_t *rid; const uint32_t *mod;
-    const int64_t *first_row; const uint32_t *n_instr;
+    const int64_t *first_row;
     long long cap_rows;
     int inline_names, header;
     char *text; unsigned long long text_cap; uint64_t *text_off; uint32_t *dis_status;
     DisCtrl *ctrl; DisMod *dm; uint32_t *arena; long long arena_words;
-    unsigned long long *tstate; uint64_t *rowpos;
+    unsigned long long *tstate;
     long long max_spins;
 };
 
-__device__ __forceinline__ int dec_len(unsigned long long v) { int n = 1; while (v >= 10) { v /= 10; n++; } return n; }
-
-// header comment lines: "; SPIR-V\n; Version: M.m\n; Generator: 0x%08x\n; Bound: B\n; Schema: S\n"
-__device__ uint32_t header_len(const uint32_t *w)
-{
-    return 9 + (11 + dec_len((w[1] >> 16) & 0xff) + 1 + dec_len((w[1] >> 8) & 0xff) + 1) + (13 + 10 + 1) +
-           (9 + dec_len(w[3]) + 1) + (10 + dec_len(w[4]) + 1);
-}
-
-// Per-module id tables: for every id the module-local row of its first
-// OpName and of its first definition. Direct tables of 2 * bound words when
-// bound <= 2 * len + 64; otherwise a hash map of len + 64 ids (keys, then
-// name rows, then definition rows; empty key 0xFFFFFFFF). A module of len
-// words names or defines fewer than len ids, so the map never fills.
+// ---------------------------------------------------------------------------
+// per-module id tables
+// ---------------------------------------------------------------------------
+// Direct table of 3 words per id [name row, name length, definition row]
+// when bound <= len + 64; otherwise a hash map of len + 64 slots of 4 words
+// [id, name row, name length, definition row] (empty id 0xFFFFFFFF). A
+// module of len words names or defines fewer than len ids, so the map never
+// fills, and a huge bound in a header costs nothing.
 __host__ __device__ inline bool idtab_dense(uint32_t bound, long long len)
 {
-    return (unsigned long long)bound <= 2ull * (unsigned long long)len + 64;
+    return (unsigned long long)bound <= (unsigned long long)len + 64;
 }
 __host__ __device__ inline unsigned long long idtab_words(uint32_t bound, long long len)
 {
-    return idtab_dense(bound, len) ? 2ull * bound : 3ull * ((unsigned long long)len + 64);
+    return idtab_dense(bound, len) ? 3ull * bound : 4ull * ((unsigned long long)len + 64);
 }
-__device__ __forceinline__ uint32_t idtab_hash(uint32_t id, uint32_t slots) { return (uint32_t)(((unsigned long long)id * 2654435761ull) % slots); }
-// slot of id (id < bound), or -1 when absent (create = false)
-__device__ __forceinline__ long long idtab_slot(uint32_t *base, uint32_t bound, uint32_t slots, uint32_t id, bool create)
+// the id's [name row, name length, def row] triple, or null when absent
+__device__ __forceinline__ uint32_t *idtab_entry(uint32_t *base, uint32_t bound, uint32_t slots, uint32_t id,
+                                                 bool create)
 {
-    if (!slots) return id < bound ? (long long)id : -1;
-    uint32_t h = idtab_hash(id, slots);
+    if (!slots) return id < bound ? base + 3ull * id : nullptr;
+    uint32_t h = (uint32_t)(((unsigned long long)id * 2654435761ull) % slots);
     for (;;) {
-        uint32_t k = create ? atomicCAS(&base[h], NOROW, id) : base[h];
-        if (k == id || (create && k == NOROW)) return h;
-        if (k == NOROW) return -1;
+        uint32_t *e = base + 4ull * h;
+        uint32_t k = create ? atomicCAS(e, NOROW, id) : e[0];
+        if (k == id || (create && k == NOROW)) return e + 1;
+        if (k == NOROW) return nullptr;
         h = h + 1 == slots ? 0 : h + 1;
     }
 }
-__device__ __forceinline__ uint32_t *idtab_names(uint32_t *base, uint32_t bound, uint32_t slots) { return slots ? base + slots : base; }
-__device__ __forceinline__ uint32_t *idtab_defs(uint32_t *base, uint32_t bound, uint32_t slots) { return slots ? base + 2ull * slots : base + bound; }
+
+// header comment lines: "; SPIR-V\n; Version: M.m\n; Generator: 0x%08x\n; Bound: B\n; Schema: S\n"
+__device__ __forceinline__ uint32_t dec_len32(uint32_t v)
+{
+    return 1u + (v >= 10u) + (v >= 100u) + (v >= 1000u) + (v >= 10000u) + (v >= 100000u) + (v >= 1000000u) +
+           (v >= 10000000u) + (v >= 100000000u) + (v >= 1000000000u);
+}
+__device__ __forceinline__ uint32_t dec_len64(unsigned long long v)
+{
+    if (!(v >> 32)) return dec_len32((uint32_t)v);
+    uint32_t n = 10;
+    unsigned long long t = 10000000000ull;
+    while (n < 20 && v >= t) { n++; t *= 10; }
+    return n;
+}
+__device__ uint32_t header_len(const uint32_t *w)
+{
+    return 9 + (11 + dec_len32((w[1] >> 16) & 0xff) + 1 + dec_len32((w[1] >> 8) & 0xff) + 1) + (13 + 10 + 1) +
+           (9 + dec_len32(w[3]) + 1) + (10 + dec_len32(w[4]) + 1);
+}
 
 // ---------------------------------------------------------------------------
-// sinks
+// sinks: the formatter below runs once counting, once writing
 // ---------------------------------------------------------------------------
 struct CountSink {
-    unsigned long long n = 0;
-    __device__ void put(char) { n++; }
-    __device__ void puts(const char *s, int len) { n += len; }
+    static constexpr bool counting = true;
+    uint32_t n = 0;
+    __device__ __forceinline__ void put(char) { n++; }
+    __device__ __forceinline__ void puts(const char *, int len) { n += len; }
 };
 struct WriteSink {
+    static constexpr bool counting = false;
     char *p;
-    __device__ void put(char c) { *p++ = c; }
-    __device__ void puts(const char *s, int len) { for (int i = 0; i < len; i++) p[i] = s[i]; p += len; }
+    __device__ __forceinline__ void put(char c) { *p++ = c; }
+    __device__ __forceinline__ void puts(const char *s, int len) { for (int i = 0; i < len; i++) p[i] = s[i]; p += len; }
 };
 
-template <class Sink> __device__ void put_lit(Sink &k, const char *s)
+template <class Sink> __device__ __forceinline__ void put_lit(Sink &k, const char *s)
 {
     int n = 0;
     while (s[n]) n++;
     k.puts(s, n);
 }
-template <class Sink> __device__ void put_dec(Sink &k, unsigned long long v)
+template <class Sink> __device__ __forceinline__ void put_dec(Sink &k, unsigned long long v)
 {
-    char b[20];
-    int n = 0;
-    do { b[n++] = (char)('0' + v % 10); v /= 10; } while (v);
-    while (n) k.put(b[--n]);
-}
-template <class Sink> __device__ void put_hex_digits(Sink &k, unsigned long long v, int digits)
-{
-    for (int i = digits - 1; i >= 0; i--) {
-        unsigned d = (unsigned)((v >> (4 * i)) & 15);
-        k.put((char)(d < 10 ? '0' + d : 'a' + d - 10));
+    if constexpr (Sink::counting) {
+        k.n += dec_len64(v);
+    } else {
+        // digits written backwards into place: no local buffer
+        uint32_t n = dec_len64(v);
+        char *e = k.p + n;
+        if (!(v >> 32)) {
+            uint32_t x = (uint32_t)v;
+            do { *--e = (char)('0' + x % 10u); x /= 10u; } while (x);
+        } else {
+            do { *--e = (char)('0' + v % 10); v /= 10; } while (v);
+        }
+        k.p += n;
     }
 }
-template <class Sink> __device__ void put_hex8(Sink &k, uint32_t v) { k.put('0'); k.put('x'); put_hex_digits(k, v, 8); }
-template <class Sink> __device__ void put_name(Sink &k, uint16_t off, uint8_t len)
+template <class Sink> __device__ __forceinline__ void put_hex_digits(Sink &k, unsigned long long v, int digits)
+{
+    if constexpr (Sink::counting) {
+        k.n += digits;
+    } else {
+        for (int i = digits - 1; i >= 0; i--) {
+            unsigned d = (unsigned)((v >> (4 * i)) & 15);
+            k.put((char)(d < 10 ? '0' + d : 'a' + d - 10));
+        }
+    }
+}
+template <class Sink> __device__ __forceinline__ void put_hex8(Sink &k, uint32_t v)
+{
+    k.put('0'); k.put('x'); put_hex_digits(k, v, 8);
+}
+template <class Sink> __device__ __forceinline__ void put_name(Sink &k, uint16_t off, uint8_t len)
 {
     k.puts(g_spv_tables.names + off, len);
 }
@@ -139,14 +183,14 @@ template <class Sink> __device__ void put_name(Sink &k, uint16_t off, uint8_t le
 // for normal numbers (trailing zero digits dropped, no point when none are
 // left), [-]0x0.<hex>p-1022 for subnormals, [-]0x0p+0 for zero, [-]inf and
 // [-]nan.
-template <class Sink> __device__ void put_hexfloat64(Sink &k, unsigned long long b)
+template <class Sink> __device__ __noinline__ Sink put_hexfloat64(Sink k, unsigned long long b)
 {
     bool neg = b >> 63;
     unsigned e = (unsigned)((b >> 52) & 0x7ff);
     unsigned long long m = b & ((1ull << 52) - 1);
-    if (e == 0x7ff) { if (neg) k.put('-'); put_lit(k, m ? "nan" : "inf"); return; }
+    if (e == 0x7ff) { if (neg) k.put('-'); put_lit(k, m ? "nan" : "inf"); return k; }
     if (neg) k.put('-');
-    if (e == 0 && m == 0) { put_lit(k, "0x0p+0"); return; }
+    if (e == 0 && m == 0) { put_lit(k, "0x0p+0"); return k; }
     k.put('0'); k.put('x'); k.put(e == 0 ? '0' : '1');
     if (m) {
         int digits = 13;
@@ -158,6 +202,7 @@ template <class Sink> __device__ void put_hexfloat64(Sink &k, unsigned long long
     int ex = e == 0 ? -1022 : (int)e - 1023;
     if (ex < 0) { k.put('-'); ex = -ex; } else k.put('+');
     put_dec(k, (unsigned long long)ex);
+    return k;
 }
 
 // a 32-bit float widened exactly to double bits
@@ -183,55 +228,58 @@ struct RowCtx {
     const uint32_t *iw;          // the instruction's words
     uint32_t wc, op;
     const DisMod *md;
-    uint32_t *tab;               // module's id tables
-    bool names;                  // inline names on
+    uint32_t *tab;               // the module's id table
     const DP *P;
     int64_t first;               // module's first row
+    bool walk_ok;
 };
 
 template <class Sink> __device__ void put_id(Sink &k, const RowCtx &c, uint32_t id)
 {
     k.put('%');
-    if (c.names && id < c.md->bound) {
-        long long sl = idtab_slot(c.tab, c.md->bound, c.md->slots, id, false);
-        uint32_t nr = sl < 0 ? NOROW : idtab_names(c.tab, c.md->bound, c.md->slots)[sl];
+    if (c.P->inline_names && id < c.md->bound) {
+        const uint32_t *e = idtab_entry(c.tab, c.md->bound, c.md->slots, id, false);
+        uint32_t nr = e ? e[0] : NOROW;
         if (nr != NOROW) {
-            int64_t row = c.first + nr;
-            const uint32_t *nw = c.P->words + c.P->off[row];
-            uint32_t nwc = c.P->wc[row];
-            bool stop = false;
-            for (uint32_t i = 2; i < nwc && !stop; i++) {
-                uint32_t v = __ldg(nw + i);
-                for (int b = 0; b < 4; b++) {
-                    unsigned ch = (v >> (8 * b)) & 0xffu;
-                    if (!ch) { stop = true; break; }
-                    bool keep = (ch >= '0' && ch <= '9') || (ch >= 'A' && ch <= 'Z') || (ch >= 'a' && ch <= 'z') || ch == '_';
-                    k.put(keep ? (char)ch : '_');
+            if constexpr (Sink::counting) {
+                k.n += e[1] + 1;
+            } else {
+                int64_t row = c.first + nr;
+                const uint32_t *nw = c.P->words + c.P->off[row];
+                uint32_t left = e[1];
+                for (uint32_t i = 2; left; i++) {
+                    uint32_t v = __ldg(nw + i);
+                    for (int b = 0; b < 4 && left; b++, left--) {
+                        unsigned ch = (v >> (8 * b)) & 0xffu;
+                        bool keep = (ch >= '0' && ch <= '9') || (ch >= 'A' && ch <= 'Z') || (ch >= 'a' && ch <= 'z') || ch == '_';
+                        k.put(keep ? (char)ch : '_');
+                    }
                 }
+                k.put('_');
             }
-            k.put('_');
         }
     }
     put_dec(k, id);
 }
 
-template <class Sink> __device__ void put_string(Sink &k, const uint32_t *iw, uint32_t pos, uint32_t n)
+template <class Sink> __device__ __noinline__ Sink put_string(Sink k, const uint32_t *iw, uint32_t pos, uint32_t n)
 {
     k.put('"');
     for (uint32_t i = 0; i < n; i++) {
         uint32_t v = __ldg(iw + pos + i);
         for (int b = 0; b < 4; b++) {
             unsigned ch = (v >> (8 * b)) & 0xffu;
-            if (!ch) { k.put('"'); return; }
+            if (!ch) { k.put('"'); return k; }
             if (ch == '"' || ch == '\\') { k.put('\\'); k.put((char)ch); }
             else if (ch < 0x20 || ch > 0x7e) { k.put('\\'); k.put('x'); put_hex_digits(k, ch, 2); }
             else k.put((char)ch);
         }
     }
     k.put('"');
+    return k;
 }
 
-template <class Sink> __device__ void put_venum(Sink &k, int kind, uint32_t v)
+template <class Sink> __device__ __forceinline__ void put_venum(Sink &k, int kind, uint32_t v)
 {
     if (v < 64 && g_spv_tables.venum[kind][v].known) {
         const spvt::EnDesc &e = g_spv_tables.venum[kind][v];
@@ -257,9 +305,14 @@ template <class Sink> __device__ void put_benum(Sink &k, int kind, uint32_t v)
     }
 }
 
-template <class Sink> __device__ void put_raw_tail(Sink &k, const RowCtx &c)
+template <class Sink> __device__ __noinline__ Sink put_raw_tail(Sink k, const uint32_t *iw, uint32_t wc)
 {
-    for (uint32_t i = 1; i < c.wc; i++) { k.put(' '); put_hex8(k, __ldg(c.iw + i)); }
+    if constexpr (Sink::counting) {
+        k.n += 11 * (wc - 1);
+    } else {
+        for (uint32_t i = 1; i < wc; i++) { k.put(' '); put_hex8(k, __ldg(iw + i)); }
+    }
+    return k;
 }
 
 // one operand of a parameter list (no optional / repeat forms except A_LITS)
@@ -270,8 +323,27 @@ template <class Sink> __device__ void put_param(Sink &k, const RowCtx &c, uint8_
     k.put(' ');
     if (pc == spvt::A_ID) { put_id(k, c, word(pos)); pos++; }
     else if (pc == spvt::A_LIT) { put_dec(k, word(pos)); pos++; }
-    else if (pc == spvt::A_STR) { uint32_t n = string_words(word, pos, c.wc); put_string(k, c.iw, pos, n); pos += n; }
+    else if (pc == spvt::A_STR) { uint32_t n = string_words(word, pos, c.wc); k = put_string(k, c.iw, pos, n); pos += n; }
     else { put_venum(k, pc - spvt::A_ENUM, word(pos)); pos++; }
+}
+
+template <class Sink> __device__ __noinline__ Sink put_ctx_literal(Sink k, RowCtx c, uint32_t rt, uint32_t pos)
+{
+    auto word = [&](uint32_t i) -> uint32_t { return __ldg(c.iw + i); };
+    uint32_t n = c.wc - pos;
+    bool is_float = false;
+    if (rt < c.md->bound) {
+        const uint32_t *e = idtab_entry(c.tab, c.md->bound, c.md->slots, rt, false);
+        uint32_t dr = e ? e[2] : NOROW;
+        if (dr != NOROW && c.P->op[c.first + dr] == 22) is_float = true;
+    }
+    k.put(' ');
+    if (is_float && n == 1) k = put_hexfloat64(k, f32_to_f64_bits(word(pos)));
+    else if (is_float && n == 2) k = put_hexfloat64(k, (unsigned long long)word(pos) | ((unsigned long long)word(pos + 1) << 32));
+    else if (n == 1) put_dec(k, word(pos));
+    else if (n == 2) put_dec(k, (unsigned long long)word(pos) | ((unsigned long long)word(pos + 1) << 32));
+    else for (uint32_t i = 0; i < n; i++) { if (i) k.put(' '); put_dec(k, word(pos + i)); }
+    return k;
 }
 
 template <class Sink> __device__ void format_row(Sink &k, const RowCtx &c)
@@ -280,14 +352,13 @@ template <class Sink> __device__ void format_row(Sink &k, const RowCtx &c)
     auto word = [&](uint32_t i) -> uint32_t { return __ldg(c.iw + i); };
     if (c.op >= 256 || !(T.ops[c.op].flags & 1)) {
         k.put('O'); k.put('p'); put_dec(k, c.op);
-        put_raw_tail(k, c); k.put('\n');
+        k = put_raw_tail(k, c.iw, c.wc); k.put('\n');
         return;
     }
     const spvt::OpDesc &d = T.ops[c.op];
-    Walk wk = walk_instruction(word, c.wc, d, 0xffffffffu);
-    if (!wk.ok) {
+    if (!c.walk_ok) {
         put_name(k, d.name_off, d.name_len);
-        put_raw_tail(k, c); k.put('\n');
+        k = put_raw_tail(k, c.iw, c.wc); k.put('\n');
         return;
     }
     uint32_t pos = 1;
@@ -307,21 +378,9 @@ template <class Sink> __device__ void format_row(Sink &k, const RowCtx &c)
         else if (code == spvt::A_LIT) { k.put(' '); put_dec(k, word(pos)); pos++; }
         else if (code == spvt::A_STR) {
             uint32_t n = string_words(word, pos, c.wc);
-            k.put(' '); put_string(k, c.iw, pos, n); pos += n;
+            k.put(' '); k = put_string(k, c.iw, pos, n); pos += n;
         } else if (code == spvt::A_CTX) {
-            uint32_t n = c.wc - pos;
-            bool is_float = false;
-            if (rt < c.md->bound) {
-                long long sl = idtab_slot(c.tab, c.md->bound, c.md->slots, rt, false);
-                uint32_t dr = sl < 0 ? NOROW : idtab_defs(c.tab, c.md->bound, c.md->slots)[sl];
-                if (dr != NOROW && c.P->op[c.first + dr] == 22) is_float = true;
-            }
-            k.put(' ');
-            if (is_float && n == 1) put_hexfloat64(k, f32_to_f64_bits(word(pos)));
-            else if (is_float && n == 2) put_hexfloat64(k, (unsigned long long)word(pos) | ((unsigned long long)word(pos + 1) << 32));
-            else if (n == 1) put_dec(k, word(pos));
-            else if (n == 2) put_dec(k, (unsigned long long)word(pos) | ((unsigned long long)word(pos + 1) << 32));
-            else for (uint32_t i = 0; i < n; i++) { if (i) k.put(' '); put_dec(k, word(pos + i)); }
+            k = put_ctx_literal(k, c, rt, pos);
             pos = c.wc;
         } else if (code >= spvt::A_ENUM && code < spvt::A_ENUM + spvt::NUM_VKINDS) {
             int kind = code - spvt::A_ENUM;
@@ -352,27 +411,20 @@ template <class Sink> __device__ void format_row(Sink &k, const RowCtx &c)
     k.put('\n');
 }
 
-__device__ __forceinline__ bool make_ctx(const DP &P, long long row, RowCtx &c)
+template <class Sink> __device__ void format_header(Sink &k, const uint32_t *w)
 {
-    uint32_t m = P.mod[row];
-    const DisMod &md = P.dm[m];
-    if (!md.ok) return false;
-    c.iw = P.words + P.off[row];
-    c.wc = P.wc[row];
-    c.op = P.op[row];
-    c.md = &md;
-    c.tab = P.arena + md.arena_off;
-    c.names = P.inline_names != 0;
-    c.P = &P;
-    c.first = P.first_row[m];
-    return true;
+    put_lit(k, "; SPIR-V\n; Version: ");
+    put_dec(k, (w[1] >> 16) & 0xff); k.put('.'); put_dec(k, (w[1] >> 8) & 0xff);
+    put_lit(k, "\n; Generator: "); put_hex8(k, w[2]);
+    put_lit(k, "\n; Bound: "); put_dec(k, w[3]);
+    put_lit(k, "\n; Schema: "); put_dec(k, w[4]); k.put('\n');
 }
 
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
 // chunked block-wide exclusive scan over modules (1024 threads): calls
-// f(m, excl) for every module with the exclusive prefix of val(m)
+// f(m, excl, v) for every module with the exclusive prefix of val(m)
 template <class Val, class F>
 __device__ unsigned long long block_scan_modules(int n_mod, Val val, F f)
 {
@@ -405,7 +457,8 @@ __device__ unsigned long long block_scan_modules(int n_mod, Val val, F f)
 
 __global__ void __launch_bounds__(1024) k_dis_prepass(DP P)
 {
-    // pass A: header status, bound, id-table arena layout
+    long long n_rows = P.first_row[P.n_mod];
+    if (n_rows > P.cap_rows) n_rows = P.cap_rows;
     unsigned long long used = block_scan_modules(P.n_mod,
         [&](int m) -> unsigned long long {
             long long o = P.mod_off[m], len = P.mod_off[m + 1] - o;
@@ -422,17 +475,15 @@ __global__ void __launch_bounds__(1024) k_dis_prepass(DP P)
             d.ok = st == S_OK && (long long)(excl + na) <= P.arena_words;
             d.status = st != S_OK ? st : (d.ok ? S_OK : S_CAPACITY);
             d.header_len = (d.ok && P.header) ? header_len(P.words + o) : 0;
-            d.hincl = 0;
+            d.pad = 0;
+            long long fr = P.first_row[m];
+            d.item_base = (fr < n_rows ? fr : n_rows) + m;
             P.dm[m] = d;
         });
-    // pass B: inclusive scan of the header bytes of the modules that print
-    block_scan_modules(P.n_mod,
-        [&](int m) -> unsigned long long { return P.dm[m].header_len; },
-        [&](int m, unsigned long long excl, unsigned long long nh) { P.dm[m].hincl = excl + nh; });
     if (threadIdx.x == 0) {
         P.ctrl->arena_used = used < (unsigned long long)P.arena_words ? used : (unsigned long long)P.arena_words;
-        long long nr = P.first_row[P.n_mod];
-        P.ctrl->n_rows = (unsigned long long)(nr < P.cap_rows ? nr : P.cap_rows);
+        P.ctrl->n_rows = (unsigned long long)n_rows;
+        P.ctrl->n_items = (unsigned long long)n_rows + P.n_mod;
         P.ctrl->next_tile = 0;
         P.ctrl->timeout = 0;
     }
@@ -441,7 +492,7 @@ __global__ void __launch_bounds__(1024) k_dis_prepass(DP P)
 __global__ void k_dis_clear(DP P)
 {
     unsigned long long n = P.ctrl->arena_used;
-    unsigned long long nt = P.ctrl->n_rows / DROWS + 1;
+    unsigned long long nt = P.ctrl->n_items / ITEMS + 1;
     long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)n; i += stride) P.arena[i] = NOROW;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)nt; i += stride) P.tstate[i] = 0;
@@ -462,61 +513,196 @@ __global__ void k_dis_ids(DP P)
         uint32_t *tab = P.arena + md.arena_off;
         if (op == 5 && wc >= 2 && P.inline_names) {
             uint32_t target = __ldg(P.words + P.off[row] + 1);
-            if (target < md.bound) {
-                long long sl = idtab_slot(tab, md.bound, md.slots, target, true);
-                atomicMin(&idtab_names(tab, md.bound, md.slots)[sl], local);
-            }
+            if (target < md.bound) atomicMin(&idtab_entry(tab, md.bound, md.slots, target, true)[0], local);
         }
         if (op < 256 && (T.ops[op].flags & 4)) {
             uint32_t q = 1 + ((T.ops[op].flags >> 1) & 1);
             if (q < wc) {
                 uint32_t id = P.rid[row];
-                if (id < md.bound) {
-                    long long sl = idtab_slot(tab, md.bound, md.slots, id, true);
-                    atomicMin(&idtab_defs(tab, md.bound, md.slots)[sl], local);
-                }
+                if (id < md.bound) atomicMin(&idtab_entry(tab, md.bound, md.slots, id, true)[2], local);
             }
         }
     }
 }
 
-// pass 1: byte count per row, scanned into 64-bit positions
-__global__ void __launch_bounds__(DNT) k_dis_len(DP P)
+// name length of each id's first OpName: its string's bytes before the first
+// NUL, or to the instruction's end
+__global__ void k_dis_namelen(DP P)
 {
-    __shared__ unsigned long long s_w[DNT / 32];
-    __shared__ unsigned long long s_base;
-    __shared__ long long s_tile;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const long long n = (long long)P.ctrl->n_rows;
-    const long long ntiles = n / DROWS + 1;
-    for (;;) {
-        if (tid == 0) s_tile = (long long)atomicAdd(&P.ctrl->next_tile, 1u);
-        __syncthreads();
-        long long t = s_tile;
-        if (t >= ntiles) break;
-        unsigned long long len[DPT];
-        unsigned long long mine = 0;
-        #pragma unroll
-        for (int i = 0; i < DPT; i++) {
-            long long row = t * DROWS + (long long)tid * DPT + i;
-            len[i] = 0;
-            if (row < n) {
-                RowCtx c;
-                if (make_ctx(P, row, c)) { CountSink k; format_row(k, c); len[i] = k.n; }
-            }
-            mine += len[i];
+    if (!P.inline_names) return;
+    long long n = (long long)P.ctrl->n_rows;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < n; row += stride) {
+        if (P.op[row] != 5) continue;
+        uint32_t wc = P.wc[row];
+        if (wc < 2) continue;
+        uint32_t m = P.mod[row];
+        const DisMod &md = P.dm[m];
+        if (!md.ok) continue;
+        const uint32_t *iw = P.words + P.off[row];
+        uint32_t target = __ldg(iw + 1);
+        if (target >= md.bound) continue;
+        uint32_t *e = idtab_entry(P.arena + md.arena_off, md.bound, md.slots, target, false);
+        if (!e || e[0] != (uint32_t)(row - P.first_row[m])) continue;
+        uint32_t len = 0;
+        for (uint32_t i = 2; i < wc; i++) {
+            uint32_t v = __ldg(iw + i);
+            uint32_t z = (v - 0x01010101u) & ~v & 0x80808080u;
+            if (z) { len += (uint32_t)((__ffs(z) - 1) >> 3); break; }
+            len += 4;
         }
-        unsigned long long incl = mine;
-        #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) { unsigned long long v = __shfl_up_sync(0xffffffffu, incl, d); if (lane >= d) incl += v; }
-        if (lane == 31) s_w[wid] = incl;
+        e[1] = len;
+    }
+}
+
+constexpr int NSHAPE = 64;
+
+struct MainSmem {
+    char text[TEXT_SMEM + 16];
+    long long ibase[ITEMS + 2];     // item_base of modules m0 .. m0 + nm, then the next module's (or n_items)
+    long long irow[ITEMS];          // per item of the tile: its row, -1 for a header item
+    int im[ITEMS];                  // per item: its module, -1 past the end
+    uint32_t ilen[ITEMS];           // per item: text bytes
+    uint32_t ioff[ITEMS];           // per item: offset in the tile's text
+    uint16_t perm[ITEMS];           // items grouped by text shape
+    uint16_t rank[ITEMS];           // per item: position within its shape group
+    uint8_t icls[ITEMS];            // per item: shape class
+    uint8_t iok[ITEMS];             // per item: operands parse (else raw words)
+    uint32_t cls_n[NSHAPE];
+    uint32_t warp_tot[DNT / 32];
+    long long tile;
+    unsigned long long base;
+    int m0, nm;
+    int gave_up;
+};
+
+__device__ __forceinline__ bool make_ctx(const DP &P, int m, long long row, RowCtx &c, int walk_ok)
+{
+    const DisMod &md = P.dm[m];
+    if (!md.ok) return false;
+    c.iw = P.words + P.off[row];
+    c.wc = P.wc[row];
+    c.op = P.op[row];
+    c.md = &md;
+    c.tab = P.arena + md.arena_off;
+    c.P = &P;
+    c.first = P.first_row[m];
+    if (walk_ok >= 0) c.walk_ok = walk_ok != 0;
+    else {
+        c.walk_ok = true;
+        if (c.op < 256 && (g_spv_tables.ops[c.op].flags & 1)) {
+            auto word = [&](uint32_t i) -> uint32_t { return __ldg(c.iw + i); };
+            c.walk_ok = walk_instruction(word, c.wc, g_spv_tables.ops[c.op], 0xffffffffu).ok;
+        }
+    }
+    return true;
+}
+
+// One tile of items: locate, group by text shape (so the lines a warp
+// formats share their control flow), measure, scan, format, copy out.
+__global__ void __launch_bounds__(DNT) k_dis_main(DP P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MainSmem &s = *reinterpret_cast<MainSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const long long n_items = (long long)P.ctrl->n_items;
+    const long long ntiles = (n_items + ITEMS - 1) / ITEMS;
+    for (;;) {
+        if (tid == 0) {
+            s.tile = (long long)atomicAdd(&P.ctrl->next_tile, 1u);
+            s.gave_up = 0;
+            if (s.tile < ntiles) {
+                long long i0 = s.tile * ITEMS;
+                int lo = 0, hi = P.n_mod;            // last module whose header item is <= i0
+                while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (P.dm[mid].item_base <= i0) lo = mid; else hi = mid; }
+                s.m0 = lo;
+                int nm = P.n_mod - lo;
+                s.nm = nm < ITEMS + 1 ? nm : ITEMS + 1;
+            }
+        }
+        if (tid < NSHAPE) s.cls_n[tid] = 0;
         __syncthreads();
-        if (wid == 0) {
-            unsigned long long v = lane < DNT / 32 ? s_w[lane] : 0;
+        const long long t = s.tile;
+        if (t >= ntiles) break;
+        const long long i0 = t * ITEMS;
+        const int m0 = s.m0, nm = s.nm;
+        for (int j = tid; j <= nm; j += DNT)
+            s.ibase[j] = j < nm ? P.dm[m0 + j].item_base : (m0 + nm < P.n_mod ? P.dm[m0 + nm].item_base : n_items);
+        __syncthreads();
+
+        // 1. locate every item and count the shape classes
+        for (int j = tid; j < ITEMS; j += DNT) {
+            long long i = i0 + j;
+            int m = -1, cls = 0;
+            long long row = -1;
+            if (i < n_items) {
+                int lo = 0, hi = nm;                 // last k with ibase[k] <= i
+                while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (s.ibase[mid] <= i) lo = mid; else hi = mid; }
+                m = m0 + lo;
+                if (i != s.ibase[lo]) {
+                    row = P.first_row[m] + (i - s.ibase[lo] - 1);
+                    uint32_t op = P.op[row];
+                    cls = op < 256 ? g_spv_tables.shape[op] : 1;
+                }
+            }
+            s.im[j] = m;
+            s.irow[j] = row;
+            s.icls[j] = (uint8_t)cls;
+            s.rank[j] = (uint16_t)atomicAdd(&s.cls_n[cls], 1u);
+        }
+        __syncthreads();
+        if (wid == 0) {                               // exclusive scan of the class counts
+            uint32_t a = s.cls_n[lane], b = s.cls_n[lane + 32];
+            uint32_t ia = a, ib = b;
             #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) { unsigned long long u = __shfl_up_sync(0xffffffffu, v, d); if (lane >= d) v += u; }
-            if (lane < DNT / 32) s_w[lane] = v;
-            unsigned long long total = __shfl_sync(0xffffffffu, v, DNT / 32 - 1);
+            for (int d = 1; d < 32; d <<= 1) {
+                uint32_t x = __shfl_up_sync(0xffffffffu, ia, d), y = __shfl_up_sync(0xffffffffu, ib, d);
+                if (lane >= d) { ia += x; ib += y; }
+            }
+            uint32_t tot_a = __shfl_sync(0xffffffffu, ia, 31);
+            s.cls_n[lane] = ia - a;
+            s.cls_n[lane + 32] = tot_a + ib - b;
+        }
+        __syncthreads();
+        for (int j = tid; j < ITEMS; j += DNT) s.perm[s.cls_n[s.icls[j]] + s.rank[j]] = (uint16_t)j;
+        __syncthreads();
+
+        // 2. measure, in shape order
+        for (int q = tid; q < ITEMS; q += DNT) {
+            int j = s.perm[q];
+            int m = s.im[j];
+            uint32_t len = 0;
+            uint8_t ok = 1;
+            if (m >= 0) {
+                if (s.irow[j] < 0) len = P.dm[m].header_len;
+                else {
+                    RowCtx c;
+                    if (make_ctx(P, m, s.irow[j], c, -1)) { CountSink k; format_row(k, c); len = k.n; ok = c.walk_ok; }
+                }
+            }
+            s.ilen[j] = len;
+            s.iok[j] = ok;
+        }
+        __syncthreads();
+        // 3. scan in item order (two consecutive items per thread), then the tile's base
+        {
+            uint32_t a = s.ilen[2 * tid], b = s.ilen[2 * tid + 1];
+            uint32_t mine = a + b, incl = mine;
+            #pragma unroll
+            for (int d = 1; d < 32; d <<= 1) { uint32_t v = __shfl_up_sync(0xffffffffu, incl, d); if (lane >= d) incl += v; }
+            if (lane == 31) s.warp_tot[wid] = incl;
+            __syncthreads();
+            uint32_t wpre = 0;
+            #pragma unroll
+            for (int w = 0; w < DNT / 32; w++) if (w < wid) wpre += s.warp_tot[w];
+            uint32_t ex = wpre + incl - mine;
+            s.ioff[2 * tid] = ex;
+            s.ioff[2 * tid + 1] = ex + a;
+        }
+        uint32_t total = 0;
+        #pragma unroll
+        for (int w = 0; w < DNT / 32; w++) total += s.warp_tot[w];
+        if (wid == 0) {
             unsigned long long excl = 0;
             if (t == 0) {
                 if (lane == 0) st_release(&P.tstate[0], F_INC | total);
@@ -525,8 +711,8 @@ __global__ void __launch_bounds__(DNT) k_dis_len(DP P)
                 long long hi = t - 1, spins = 0;
                 bool gave_up = false;
                 for (;;) {
-                    long long j = hi - lane;
-                    unsigned long long st = j >= 0 ? ld_acquire(&P.tstate[j]) : F_INC;
+                    long long jj = hi - lane;
+                    unsigned long long st = jj >= 0 ? ld_acquire(&P.tstate[jj]) : F_INC;
                     unsigned long long f = st & F_MSK;
                     unsigned incm = __ballot_sync(0xffffffffu, f == F_INC);
                     unsigned nonem = __ballot_sync(0xffffffffu, f == 0);
@@ -537,92 +723,80 @@ __global__ void __launch_bounds__(DNT) k_dis_len(DP P)
                         spin_pause();
                         continue;
                     }
-                    unsigned long long v2 = (lane <= le && j >= 0) ? (st & ~F_MSK) : 0ull;
+                    unsigned long long v2 = (lane <= le && jj >= 0) ? (st & ~F_MSK) : 0ull;
                     #pragma unroll
                     for (int d = 16; d > 0; d >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, d);
                     excl += v2;
                     if (incm) break;
                     hi -= 32;
                 }
-                if (gave_up && lane == 0) atomicExch(&P.ctrl->timeout, 1u);
+                if (gave_up && lane == 0) { atomicExch(&P.ctrl->timeout, 1u); s.gave_up = 1; }
                 if (lane == 0) st_release(&P.tstate[t], F_INC | (excl + total));
             }
-            if (lane == 0) s_base = excl;
+            if (lane == 0) {
+                s.base = excl;
+                if (i0 + ITEMS >= n_items) P.text_off[P.n_mod] = excl + total;
+            }
         }
         __syncthreads();
-        unsigned long long pos = s_base + (wid ? s_w[wid - 1] : 0) + incl - mine;
-        #pragma unroll
-        for (int i = 0; i < DPT; i++) {
-            long long row = t * DROWS + (long long)tid * DPT + i;
-            if (row <= n) P.rowpos[row] = pos;      // rowpos[n] = total bytes of all rows
-            pos += len[i];
+        const unsigned long long base = s.base;
+        for (int j = tid; j < ITEMS; j += DNT)
+            if (s.im[j] >= 0 && s.irow[j] < 0) P.text_off[s.im[j]] = base + s.ioff[j];
+        const bool write = !s.gave_up && base + total <= P.text_cap;
+        const bool staged = total <= (uint32_t)TEXT_SMEM;
+        // 4. format once, in shape order (into shared memory, or straight to
+        //    global memory for oversized tiles)
+        if (write) {
+            for (int q = tid; q < ITEMS; q += DNT) {
+                int j = s.perm[q];
+                if (s.im[j] < 0 || s.ilen[j] == 0) continue;
+                char *dst = staged ? s.text + s.ioff[j] : P.text + base + s.ioff[j];
+                WriteSink k{dst};
+                if (s.irow[j] < 0) format_header(k, P.words + P.mod_off[s.im[j]]);
+                else { RowCtx c; make_ctx(P, s.im[j], s.irow[j], c, s.iok[j]); format_row(k, c); }
+            }
+        }
+        __syncthreads();
+        // copy out: global words wholly inside the tile's byte range are
+        // stored whole; the partial words at either end byte by byte
+        if (write && staged && total) {
+            const unsigned long long g0 = base, g1 = base + total;
+            const unsigned long long w0 = g0 >> 2, w1 = (g1 + 3) >> 2;
+            const bool aligned = (((uintptr_t)P.text) & 3) == 0;
+            uint32_t *tw = reinterpret_cast<uint32_t *>(P.text);
+            for (unsigned long long w = w0 + tid; w < w1; w += DNT) {
+                unsigned long long gb = w << 2;
+                if (aligned && gb >= g0 && gb + 4 <= g1) {
+                    const unsigned char *src = reinterpret_cast<const unsigned char *>(s.text) + (gb - g0);
+                    tw[w] = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16) | ((uint32_t)src[3] << 24);
+                } else {
+                    for (int b = 0; b < 4; b++) {
+                        unsigned long long g = gb + b;
+                        if (g >= g0 && g < g1) P.text[g] = s.text[g - g0];
+                    }
+                }
+            }
         }
         __syncthreads();
     }
 }
 
-// module offsets, status and the capacity decision
-__global__ void k_dis_offsets(DP P)
+__global__ void k_dis_status(DP P)
 {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
-    long long n = (long long)P.ctrl->n_rows;
-    if (m < P.n_mod) {
-        const DisMod &md = P.dm[m];
-        long long fr = P.first_row[m];
-        if (fr > n) fr = n;
-        unsigned long long hexcl = md.hincl - md.header_len;
-        P.text_off[m] = P.rowpos[fr] + hexcl;
-        if (P.dis_status) P.dis_status[m] = P.ctrl->timeout ? S_TIMEOUT : md.status;
-    }
-    if (m == P.n_mod) {
-        unsigned long long h = P.n_mod ? P.dm[P.n_mod - 1].hincl : 0;
-        P.text_off[P.n_mod] = P.rowpos[n] + h;
-    }
+    if (m < P.n_mod && P.dis_status) P.dis_status[m] = P.ctrl->timeout ? S_TIMEOUT : P.dm[m].status;
 }
 
-// pass 2: write rows
-__global__ void k_dis_write_rows(DP P)
-{
-    // nothing is written when the text does not fit or a wait gave up (offsets void)
-    if (P.text_off[P.n_mod] > P.text_cap || P.ctrl->timeout) return;
-    long long n = (long long)P.ctrl->n_rows;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < n; row += stride) {
-        RowCtx c;
-        if (!make_ctx(P, row, c)) continue;
-        WriteSink k{P.text + P.rowpos[row] + P.dm[P.mod[row]].hincl};
-        format_row(k, c);
-    }
-}
-
-// header lines
-__global__ void k_dis_write_headers(DP P)
-{
-    if (P.text_off[P.n_mod] > P.text_cap || P.ctrl->timeout) return;
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= P.n_mod) return;
-    const DisMod &md = P.dm[m];
-    if (!md.ok || !P.header) return;
-    const uint32_t *w = P.words + P.mod_off[m];
-    WriteSink k{P.text + P.text_off[m]};
-    put_lit(k, "; SPIR-V\n; Version: ");
-    put_dec(k, (w[1] >> 16) & 0xff); k.put('.'); put_dec(k, (w[1] >> 8) & 0xff);
-    put_lit(k, "\n; Generator: "); put_hex8(k, w[2]);
-    put_lit(k, "\n; Bound: "); put_dec(k, w[3]);
-    put_lit(k, "\n; Schema: "); put_dec(k, w[4]); k.put('\n');
-}
-
-struct DLayout { size_t ctrl, dm, tstate, rowpos, arena, total; long long arena_words; };
+struct DLayout { size_t ctrl, dm, tstate, arena, total; long long arena_words; };
 size_t dal(size_t x) { return (x + 255) & ~size_t(255); }
 DLayout dlayout(int n_mod, long long n_words, long long rows_cap, long long arena_words)
 {
     DLayout L{};
-    L.arena_words = arena_words > 0 ? arena_words : 4 * n_words + 192LL * n_mod + 64;
+    L.arena_words = arena_words > 0 ? arena_words : 4 * n_words + 256LL * n_mod + 64;
     size_t o = 0;
     L.ctrl = o; o = dal(o + sizeof(DisCtrl));
     L.dm = o; o = dal(o + sizeof(DisMod) * (size_t)n_mod);
-    L.tstate = o; o = dal(o + 8 * (size_t)(rows_cap / DROWS + 2));
-    L.rowpos = o; o = dal(o + 8 * (size_t)(rows_cap + 1));
+    L.tstate = o; o = dal(o + 8 * (size_t)((rows_cap + n_mod) / ITEMS + 2));
     L.arena = o; o = dal(o + 4 * (size_t)L.arena_words);
     L.total = o;
     return L;
@@ -657,25 +831,35 @@ extern "C" int spv_disassemble_batch(const spv_batch *batch, const spv_table *ta
     DP P{};
     P.words = batch->words; P.mod_off = batch->mod_off; P.n_mod = batch->n_modules;
     P.op = table->op; P.wc = table->wc; P.off = table->off; P.rid = table->rid; P.mod = table->mod;
-    P.first_row = table->mod_first_row; P.n_instr = table->mod_n_instr; P.cap_rows = table->capacity_rows;
+    P.first_row = table->mod_first_row; P.cap_rows = table->capacity_rows;
     P.inline_names = opts ? opts->inline_names : 1;
     P.header = opts ? opts->header : 1;
     P.text = text; P.text_cap = text_capacity; P.text_off = text_off; P.dis_status = dis_status;
     P.ctrl = (DisCtrl *)(w + L.ctrl); P.dm = (DisMod *)(w + L.dm);
-    P.tstate = (unsigned long long *)(w + L.tstate); P.rowpos = (uint64_t *)(w + L.rowpos);
+    P.tstate = (unsigned long long *)(w + L.tstate);
     P.arena = (uint32_t *)(w + L.arena); P.arena_words = L.arena_words;
     P.max_spins = 1LL << 20;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 1;
-    int nb = (batch->n_modules + 1 + 255) / 256;
+    static bool configured[64] = {};
+    if (dev < 64 && !configured[dev]) {
+        if (cudaFuncSetAttribute(k_dis_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MainSmem)) !=
+            cudaSuccess)
+            return SPV_E_CUDA;
+        configured[dev] = true;
+    }
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dis_main, DNT, sizeof(MainSmem)) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    int nb = (batch->n_modules + 255) / 256;
     SPV_LAUNCH("k_dis_prepass", st, k_dis_prepass<<<1, 1024, 0, st>>>(P));
     SPV_LAUNCH("k_dis_clear", st, k_dis_clear<<<nsm * 4, 256, 0, st>>>(P));
     SPV_LAUNCH("k_dis_ids", st, k_dis_ids<<<nsm * 8, 256, 0, st>>>(P));
-    SPV_LAUNCH("k_dis_len", st, k_dis_len<<<nsm * 4, DNT, 0, st>>>(P));
-    SPV_LAUNCH("k_dis_offsets", st, k_dis_offsets<<<nb, 256, 0, st>>>(P));
-    SPV_LAUNCH("k_dis_write_rows", st, k_dis_write_rows<<<nsm * 8, 256, 0, st>>>(P));
-    SPV_LAUNCH("k_dis_write_headers", st, k_dis_write_headers<<<nb, 256, 0, st>>>(P));
+    SPV_LAUNCH("k_dis_namelen", st, k_dis_namelen<<<nsm * 8, 256, 0, st>>>(P));
+    SPV_LAUNCH("k_dis_main", st, k_dis_main<<<nsm * per_sm, DNT, sizeof(MainSmem), st>>>(P));
+    SPV_LAUNCH("k_dis_status", st, k_dis_status<<<nb, 256, 0, st>>>(P));
     return cudaPeekAtLastError() == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;
 }

@@ -285,13 +285,19 @@ constexpr CapDep CAP_DEPS[] = {
     {57, 2}, {58, 19}, {59, 6}, {60, 17}};
 
 // ---- dense compiled tables ----------------------------------------------------
-struct OpDesc {            // 12 bytes
+struct OpDesc {            // 16 bytes
     uint8_t flags;         // bit0 known, bit1 has result type, bit2 has result id
     int8_t cap;            // required capability or -1
     uint8_t nprog;
     uint8_t prog[5];
     uint16_t name_off;
     uint8_t name_len;
+    // fast form, for operand lists made only of fixed ids / literals and an
+    // optional id*, literal* or (id, id)* tail: bit0 set when it applies,
+    // bits 1-2 the tail (0 none, 1 ids, 2 literals, 3 id pairs)
+    uint8_t fast;
+    uint16_t id_mask;      // bit i: word i (1 <= i <= nfixed) is an id
+    uint8_t nfixed;        // words after the first word before the tail
     uint8_t pad;
 };
 struct EnDesc {            // 8 bytes
@@ -311,6 +317,7 @@ struct Tables {
     EnDesc benum[NUM_BKINDS][32];   // bit enums, by bit index
     uint8_t vunknown[NUM_VKINDS];   // operand code used for the parameters of an unknown value (A_END: none)
     uint64_t cap_dep[64];           // bit b set in cap_dep[a]: declaring a declares b
+    uint8_t shape[256];             // text shape class: opcodes with the same operand list share one (1 = unknown)
     char names[NAME_POOL];
     int name_used;
 };
@@ -350,6 +357,28 @@ constexpr Tables build_tables()
         int np = 0;
         for (int k = 0; k < 5; k++) if (o.p[k]) d.prog[np++] = o.p[k];
         d.nprog = (uint8_t)np;
+        // fast form
+        {
+            bool fast = true;
+            int nfixed = 0, tail = 0;
+            uint16_t mask = 0;
+            if (o.rt) { nfixed++; mask |= (uint16_t)(1u << nfixed); }
+            if (o.rid) { nfixed++; mask |= (uint16_t)(1u << nfixed); }
+            for (int k = 0; k < np; k++) {
+                uint8_t c = d.prog[k];
+                if (tail) { fast = false; break; }
+                if (c == A_ID) { nfixed++; mask |= (uint16_t)(1u << nfixed); }
+                else if (c == A_LIT) { nfixed++; }
+                else if (c == A_IDS) tail = 1;
+                else if (c == A_LITS) tail = 2;
+                else if (c == A_IDPAIRS) tail = 3;
+                else { fast = false; break; }
+            }
+            if (nfixed > 15) fast = false;
+            d.fast = fast ? (uint8_t)(1 | (tail << 1)) : 0;
+            d.id_mask = fast ? mask : 0;
+            d.nfixed = fast ? (uint8_t)nfixed : 0;
+        }
         int len = cstrlen(o.name);
         d.name_off = (uint16_t)t.name_used;
         d.name_len = (uint8_t)len;
@@ -374,6 +403,22 @@ constexpr Tables build_tables()
     t.vunknown[K_ExecutionMode] = A_LITS;
     t.vunknown[K_Decoration] = A_LITS;
     for (const CapDep &c : CAP_DEPS) t.cap_dep[c.a] |= 1ull << c.b;
+    // shape classes: 0 is kept for module header lines, 1 for unknown opcodes
+    int next_shape = 2;
+    for (int o = 0; o < 256; o++) {
+        t.shape[o] = 1;
+        const OpDesc &d = t.ops[o];
+        if (!(d.flags & 1)) continue;
+        int found = -1;
+        for (int q = 0; q < o && found < 0; q++) {
+            const OpDesc &e = t.ops[q];
+            if (!(e.flags & 1) || e.flags != d.flags || e.nprog != d.nprog) continue;
+            bool same = true;
+            for (int k = 0; k < d.nprog; k++) if (e.prog[k] != d.prog[k]) same = false;
+            if (same) found = t.shape[q];
+        }
+        t.shape[o] = (uint8_t)(found >= 0 ? found : next_shape++);
+    }
     return t;
 }
 

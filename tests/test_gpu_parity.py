@@ -338,3 +338,25 @@ def test_full_size_large_module_and_text(gpu):
     assert g["status"][0] == st[0] == 0
     assert np.array_equal(g["out"], w)
     check_dis(gpu, w, off, g, modes=((True, True),))
+
+
+def test_every_opcode_word_counts_and_operands(gpu):
+    """Every table opcode (and a few unknown ones) at word counts 1-8 with
+    operand words in range, zero, at the bound and far above it, inserted
+    into a valid module: the status and error row equal the oracle's."""
+    base = H.minimal_body()
+    ops = oracle.opcodes() + [2, 4, 9999]
+    rng = np.random.default_rng(17)
+    mods = []
+    for op in ops:
+        for wc in range(1, 9):
+            for variant in range(3):
+                vals = []
+                for i in range(wc - 1):
+                    pick = rng.integers(0, 6) if variant else 1
+                    vals.append([3, 1, 0, 50, 0x41424344, int(rng.integers(1, 50))][int(pick)])
+                b = list(base)
+                b.insert(5, [(wc << 16) | op] + vals)
+                mods.append(H.module(b, bound=50))
+    words, offs = H.batch(mods)
+    check(gpu, words, offs, dis=True)
