@@ -241,6 +241,67 @@ int spv_disassemble_batch(const spv_batch *batch, const spv_table *table, const 
                           char *text, uint64_t text_capacity, uint64_t *text_off, uint32_t *dis_status,
                           void *workspace, size_t workspace_bytes, int64_t arena_words, spv_stream_t stream);
 
+/*
+ * Serving: continuous batching of modules that arrive one by one, as a JIT
+ * backend produces them (the paper's use case, section 4). A server owns a
+ * device pool and a pinned host pool. Submitted modules wait in a queue; a
+ * scheduler thread takes every waiting module (up to max_batch_modules /
+ * max_batch_words) as soon as a batch slot is free and runs decode +
+ * validate + disassembly on it as one batch (spv_process_batch and
+ * spv_disassemble_batch), on two streams so that the copies of one batch
+ * overlap the kernels of the next. Requests that arrive while a batch is on
+ * the GPU go into the next one. Admission is by footprint: a module of n
+ * words holds 28 * n + 64 bytes of the device pool (its words and decoded
+ * table) from submit until release; a submit that would exceed
+ * hbm_cap_bytes returns SPV_E_BUSY and changes nothing. Results (status,
+ * error row, text on the host, and the decoded rows still on the device)
+ * are owned by the server until spv_serve_release.
+ */
+#define SPV_E_BUSY (-5)         /* serving: admission cap or staging space exhausted; retry later */
+
+typedef struct spv_serve_cfg {
+    uint64_t hbm_cap_bytes;     /* admission cap on device-resident bytes (0: 8 GiB) */
+    int64_t max_batch_words;    /* largest batch (0: 32M words) */
+    int32_t max_batch_modules;  /* most modules per batch (0: 4096; 1: one module per launch sequence) */
+    int32_t inline_names;       /* disassembly options (Listing 10) */
+    int32_t header;
+    int32_t device;             /* CUDA device ordinal */
+} spv_serve_cfg;
+
+typedef struct spv_result {
+    int32_t error;              /* SPV_SUCCESS, or the SPV_E_* code of a failed batch */
+    uint32_t status;            /* module status (enum spv_status) */
+    int64_t err_row;
+    uint32_t n_instr;
+    const char *text;           /* host, text_len bytes, valid until release */
+    uint64_t text_len;
+    const uint16_t *op;         /* device: this module's rows of the decoded table */
+    const uint16_t *wc;
+    const uint32_t *rtype;
+    const uint32_t *rid;
+    const uint64_t *off;        /* word offsets into words_base */
+    const uint32_t *words_base; /* device: the batch's word buffer holding this module */
+    uint64_t submit_ns;         /* CLOCK_MONOTONIC times of submit and completion */
+    uint64_t done_ns;
+    uint32_t batch_modules;     /* size of the batch the module ran in */
+} spv_result;
+
+typedef struct spv_server spv_server;
+
+/* Create a server (allocates its pools; returns NULL on failure). */
+spv_server *spv_serve_create(const spv_serve_cfg *cfg);
+/* Copy a module (host words) into the server; *ticket identifies it.
+ * SPV_E_BUSY when admitting it would exceed the cap. */
+int spv_serve_submit(spv_server *s, const uint32_t *host_words, int64_t n_words, uint64_t *ticket);
+/* 1 and *out filled when the module is done, 0 while it is pending, SPV_E_ARG for an unknown ticket. */
+int spv_serve_poll(spv_server *s, uint64_t ticket, spv_result *out);
+/* Like poll, but waits up to timeout_us microseconds. */
+int spv_serve_wait(spv_server *s, uint64_t ticket, spv_result *out, int64_t timeout_us);
+/* Release a done module's results and its share of the device pool. */
+int spv_serve_release(spv_server *s, uint64_t ticket);
+/* Stop the scheduler, wait for in-flight batches, free everything. */
+void spv_serve_destroy(spv_server *s);
+
 /* Host-side queries of the library's own opcode / enumerant tables (no GPU
  * needed). spv_op_info returns 0 and fills the outputs for a known opcode,
  * -1 otherwise; cap is the capability the opcode requires or -1. */

@@ -344,3 +344,118 @@ def profile_read(max_kernels=64):
     if n < 0:
         raise SpvError(f"spv_profile_read failed with code {n}")
     return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(n, max_kernels))}
+
+
+# ---------------------------------------------------------------------------
+# serving handle
+# ---------------------------------------------------------------------------
+SPV_E_BUSY = -5
+
+
+class SpvServeCfg(ctypes.Structure):
+    _fields_ = [("hbm_cap_bytes", ctypes.c_uint64), ("max_batch_words", ctypes.c_int64),
+                ("max_batch_modules", ctypes.c_int32), ("inline_names", ctypes.c_int32),
+                ("header", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class SpvResult(ctypes.Structure):
+    _fields_ = [("error", ctypes.c_int32), ("status", ctypes.c_uint32), ("err_row", ctypes.c_int64),
+                ("n_instr", ctypes.c_uint32), ("text", ctypes.c_void_p), ("text_len", ctypes.c_uint64),
+                ("op", P), ("wc", P), ("rtype", P), ("rid", P), ("off", P), ("words_base", P),
+                ("submit_ns", ctypes.c_uint64), ("done_ns", ctypes.c_uint64), ("batch_modules", ctypes.c_uint32)]
+
+
+def _serve_lib():
+    lib = load()
+    if not getattr(lib, "_serve_ready", False):
+        lib.spv_serve_create.restype = ctypes.c_void_p
+        lib.spv_serve_create.argtypes = [ctypes.POINTER(SpvServeCfg)]
+        lib.spv_serve_submit.restype = ctypes.c_int
+        lib.spv_serve_submit.argtypes = [P, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
+        lib.spv_serve_poll.restype = ctypes.c_int
+        lib.spv_serve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(SpvResult)]
+        lib.spv_serve_wait.restype = ctypes.c_int
+        lib.spv_serve_wait.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(SpvResult), ctypes.c_int64]
+        lib.spv_serve_release.restype = ctypes.c_int
+        lib.spv_serve_release.argtypes = [P, ctypes.c_uint64]
+        lib.spv_serve_destroy.restype = None
+        lib.spv_serve_destroy.argtypes = [P]
+        lib._serve_ready = True
+    return lib
+
+
+def spv_serve_create(cfg):
+    return _serve_lib().spv_serve_create(ctypes.byref(cfg))
+
+
+def spv_serve_submit(server, host_words_ptr, n_words, ticket):
+    return _serve_lib().spv_serve_submit(server, host_words_ptr, n_words, ctypes.byref(ticket))
+
+
+def spv_serve_poll(server, ticket, result):
+    return _serve_lib().spv_serve_poll(server, ticket, ctypes.byref(result))
+
+
+def spv_serve_wait(server, ticket, result, timeout_us):
+    return _serve_lib().spv_serve_wait(server, ticket, ctypes.byref(result), timeout_us)
+
+
+def spv_serve_release(server, ticket):
+    return _serve_lib().spv_serve_release(server, ticket)
+
+
+def spv_serve_destroy(server):
+    _serve_lib().spv_serve_destroy(server)
+
+
+class Server:
+    """Continuous-batching server (thin wrapper over spv_serve_*)."""
+
+    def __init__(self, hbm_cap_bytes=0, max_batch_words=0, max_batch_modules=0, inline_names=True, header=True,
+                 device=0):
+        cfg = SpvServeCfg(hbm_cap_bytes, max_batch_words, max_batch_modules, 1 if inline_names else 0,
+                          1 if header else 0, device)
+        self.h = spv_serve_create(cfg)
+        if not self.h:
+            raise SpvError("spv_serve_create failed")
+
+    def submit(self, words):
+        """words: contiguous uint32 numpy array. Returns a ticket, or None when busy."""
+        t = ctypes.c_uint64()
+        rc = spv_serve_submit(self.h, words.ctypes.data_as(ctypes.c_void_p), len(words), t)
+        if rc == SPV_E_BUSY:
+            return None
+        _check(rc, "spv_serve_submit")
+        return t.value
+
+    def poll(self, ticket):
+        r = SpvResult()
+        rc = spv_serve_poll(self.h, ticket, r)
+        if rc < 0:
+            raise SpvError(f"spv_serve_poll failed with code {rc}")
+        return r if rc == 1 else None
+
+    def wait(self, ticket, timeout_us=10_000_000):
+        r = SpvResult()
+        rc = spv_serve_wait(self.h, ticket, r, timeout_us)
+        if rc < 0:
+            raise SpvError(f"spv_serve_wait failed with code {rc}")
+        return r if rc == 1 else None
+
+    @staticmethod
+    def text_of(r):
+        return ctypes.string_at(r.text, r.text_len) if r.text_len else b""
+
+    def release(self, ticket):
+        _check(spv_serve_release(self.h, ticket), "spv_serve_release")
+
+    def close(self):
+        if self.h:
+            spv_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
