@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-per-module", action="store_true", help="skip the per-module comparison leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--modules", type=int, default=10_000, help="modules in the batch workload")
+    ap.add_argument("--serve-rate", type=float, default=20_000.0, help="Poisson arrival rate of the serve leg (modules/s)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="duration of the serve leg (0: skip)")
     return ap.parse_args()
 
 
@@ -135,6 +137,62 @@ def algorithmic_bytes(kernel, W, N, L, M):
         "k_dis_namelen": 4 * N,                          # op column (OpName rows are few)
         "k_dis_clear": 0, "k_tile_setup": 0, "k_prepass": 40 * M, "k_finalize": 64 * M,
     }.get(kernel, 0)
+
+
+def serve_leg(spvgpu, w_np, off_np, rate, seconds, max_batch_modules=0, pool_size=2000, cap=4 << 30):
+    """Poisson arrivals at `rate` modules/s for `seconds`, modules drawn in
+    turn from the batch workload (its size distribution). Latency: from each
+    module's scheduled arrival to its completion (library clock), so time a
+    module waited to be admitted counts too."""
+    m_total = len(off_np) - 1
+    pool = [np.ascontiguousarray(w_np[off_np[i]:off_np[i + 1]]) for i in range(min(pool_size, m_total))]
+    srv = spvgpu.Server(hbm_cap_bytes=cap, max_batch_modules=max_batch_modules)
+    # warm up the server's kernels
+    for m in pool[:8]:
+        t = srv.submit(m)
+        srv.wait(t)
+        srv.release(t)
+    rng = np.random.default_rng(12345)
+    n = max(1, int(rate * seconds))
+    arrive = np.cumsum(rng.exponential(1.0 / rate, n))
+    lat, batch_sizes = [], []
+    words_done = 0
+    busy = 0
+    pending = []
+    head = 0
+    i = 0
+    t0 = time.monotonic_ns()
+    while i < n or head < len(pending):
+        now = time.monotonic_ns() - t0
+        while i < n and arrive[i] * 1e9 <= now:
+            m = pool[i % len(pool)]
+            t = srv.submit(m)
+            if t is None:
+                busy += 1
+                break
+            pending.append((t, t0 + int(arrive[i] * 1e9), len(m)))
+            i += 1
+        progressed = False
+        while head < len(pending):
+            t, a, nw = pending[head]
+            r = srv.poll(t)
+            if r is None:
+                break
+            lat.append(r.done_ns - a)
+            batch_sizes.append(r.batch_modules)
+            words_done += nw
+            srv.release(t)
+            head += 1
+            progressed = True
+        if not progressed:
+            time.sleep(0)
+    elapsed = (time.monotonic_ns() - t0) / 1e9
+    srv.close()
+    lat_ms = np.array(lat) / 1e6
+    return {"rate_per_s": rate, "seconds": seconds, "modules": n, "p50_ms": float(np.percentile(lat_ms, 50)),
+            "p99_ms": float(np.percentile(lat_ms, 99)), "mean_batch_modules": float(np.mean(batch_sizes)),
+            "throughput_modules_per_s": n / elapsed, "gbs": 4 * words_done / elapsed / 1e9,
+            "admission_retries": busy}
 
 
 def cpu_baseline(words, mod_off, budget_s=12.0):
@@ -325,6 +383,12 @@ def main():
         cmp = {"scope": "decode+validate+encode", "batched_gbs": res["batched"], "per_module_gbs": res["per_module"],
                "speedup": res["batched"] / res["per_module"]}
 
+    serve = None
+    if args.serve_seconds > 0 and world == 1:
+        serve = {"scope": "decode+validate+disassemble per module, Poisson arrivals, latency from arrival to completion",
+                 "continuous_batching": serve_leg(spvgpu, w_np, off_np, args.serve_rate, args.serve_seconds),
+                 "one_module_per_launch": serve_leg(spvgpu, w_np, off_np, args.serve_rate,
+                                                    min(args.serve_seconds, 1.0), max_batch_modules=1)}
     if rank != 0:
         if world > 1:
             torch.distributed.barrier()
@@ -346,6 +410,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched_vs_per_module": cmp,
+        "serve": serve,
         "clocks": clk,
         "gpu_launches": launches,
     }

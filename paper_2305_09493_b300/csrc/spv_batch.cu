@@ -57,6 +57,7 @@ struct Params {
     // workspace
     Ctrl *ctrl; int64_t *tile_off; uint32_t *tile_mod; unsigned long long *tstate; uint32_t *tmap;
     unsigned long long *cstate; ModState *ms; uint32_t *arena; int64_t arena_words; uint32_t *fixlist;
+    int64_t *abase;                // [n_modules + 1] prefix of the id-set words each module asks for
     long long max_spins;
     long long stall_tile;          // test hook: this tile never publishes its look-back states (-1: none)
     int persistent;
@@ -106,13 +107,14 @@ __global__ void __launch_bounds__(1024) k_prepass(Params P, int tile_words)
         unsigned long long et = s_base_tiles + wt + it - nt, eb = s_base_arena + wb + ib - nb;
         if (m < P.n_modules) {
             P.tile_off[m] = (int64_t)et;
+            P.abase[m] = (int64_t)eb;
             ModState s;
             s.hdr = hdr; s.bound = bound; s.err_key = NO_KEY;
             s.n_cap = s.n_mm = s.n_ep = s.n_fn = 0;
             s.decl_lo = s.decl_hi = s.req_lo = s.req_hi = 0;
             s.max_rid = 0;
             s.arena_off = -1;
-            s.id_slots = 0; s.pad2 = 0;
+            s.id_slots = 0; s.n_ids = 0; s.n_set = 0; s.pad2 = 0;
             if (hdr == S_OK && P.validate && !idset_dense(bound, P.mod_off[m + 1] - P.mod_off[m]))
                 s.id_slots = (uint32_t)nb;
             if (hdr == S_OK && P.validate) {
@@ -128,6 +130,7 @@ __global__ void __launch_bounds__(1024) k_prepass(Params P, int tile_words)
     }
     if (tid == 0) {
         P.tile_off[P.n_modules] = (int64_t)s_base_tiles;
+        P.abase[P.n_modules] = (int64_t)s_base_arena;
         P.ctrl->n_tiles = s_base_tiles;
         P.ctrl->arena_used = s_base_arena < (unsigned long long)P.arena_words ? s_base_arena
                                                                               : (unsigned long long)P.arena_words;
@@ -184,7 +187,7 @@ struct TileSmem {
     int timeout;
     // aggregates flushed once per tile
     unsigned long long err_key;
-    uint32_t n_cap, n_mm, n_ep, n_fn, decl_lo, decl_hi, req_lo, req_hi, max_rid, flags;
+    uint32_t n_cap, n_mm, n_ep, n_fn, decl_lo, decl_hi, req_lo, req_hi, max_rid, flags, n_ids;
 };
 
 template <int NT, int L>
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             s.err_key = NO_KEY;
             s.n_cap = s.n_mm = s.n_ep = s.n_fn = 0;
             s.decl_lo = s.decl_hi = s.req_lo = s.req_hi = 0;
-            s.max_rid = 0; s.flags = 0;
+            s.max_rid = 0; s.flags = 0; s.n_ids = 0;
         }
         __syncthreads();
         const uint32_t len_rel = s.len_rel, tile_n = s.tile_n, k = s.k;
@@ -479,6 +482,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             const bool valid = r < tile_count;
             uint32_t ri = 0;
             uint64_t req = 0;
+            uint32_t inserted = 0;
             if (valid) {
             uint32_t p = S16[r];
             uint32_t w0 = word(p);
@@ -511,8 +515,16 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                     if (!wk.ok) atomicMin(&s.err_key, make_key(row, R_BADOP, 0));
                     else if (wk.oob) atomicMin(&s.err_key, make_key(row, R_OOB, 0));
                     else {
-                        if ((d.flags & 4) && arena_off >= 0 && idset_insert(P.arena + arena_off, id_slots, ri))
-                            atomicOr(&s.flags, MF_DUP);
+                        if ((d.flags & 4) && arena_off >= 0) {
+                            if (id_slots == 0) {
+                                // no wait on the old value: duplicates show up later as
+                                // fewer bits set than ids inserted
+                                atomicOr(&P.arena[arena_off + (ri >> 5)], 1u << (ri & 31));
+                                inserted = 1;
+                            } else if (idset_insert(P.arena + arena_off, id_slots, ri)) {
+                                atomicOr(&s.flags, MF_DUP);
+                            }
+                        }
                         req = wk.req | width_caps(iw, op, wc);
                     }
                 }
@@ -522,10 +534,12 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             uint32_t mx = __reduce_max_sync(0xffffffffu, ri);
             uint32_t rlo = __reduce_or_sync(0xffffffffu, (uint32_t)req);
             uint32_t rhi = __reduce_or_sync(0xffffffffu, (uint32_t)(req >> 32));
+            uint32_t nins = __reduce_add_sync(0xffffffffu, inserted);
             if (lane == 0) {
                 if (mx) atomicMax(&s.max_rid, mx);
                 if (rlo) atomicOr(&s.req_lo, rlo);
                 if (rhi) atomicOr(&s.req_hi, rhi);
+                if (nins) atomicAdd(&s.n_ids, nins);
             }
         }
         // 5. encode. In the fused path every field an instruction writes back
@@ -555,12 +569,43 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             if (s.req_lo) atomicOr(&ms->req_lo, s.req_lo);
             if (s.req_hi) atomicOr(&ms->req_hi, s.req_hi);
             if (s.max_rid) atomicMax(&ms->max_rid, s.max_rid);
+            if (s.n_ids) atomicAdd(&ms->n_ids, s.n_ids);
             uint32_t fl = s.flags | (s.timeout ? MF_TIMEOUT : 0u);
             if (fl) atomicOr(&ms->flags, fl);
             if (s.timeout) atomicExch(&P.ctrl->timeout, 1u);
         }
         if (!P.persistent) break;
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// bits set in each module's bitmap id set (chunks of the arena in parallel;
+// abase is the prefix of the words each module asked for)
+// ---------------------------------------------------------------------------
+__global__ void k_id_popcount(Params P)
+{
+    const long long aw = (long long)P.ctrl->arena_used;
+    const int CH = 64;
+    const long long nch = (aw + CH - 1) / CH;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nch; c += stride) {
+        long long w = c * CH, w1 = w + CH < aw ? w + CH : aw;
+        int lo = 0, hi = P.n_modules;          // last m with abase[m] <= w
+        while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (P.abase[mid] <= w) lo = mid; else hi = mid; }
+        int m = lo;
+        while (w < w1 && m < P.n_modules) {
+            long long mend = P.abase[m + 1];
+            long long e = mend < w1 ? mend : w1;
+            const ModState &ms = P.ms[m];
+            if (e > w && ms.arena_off >= 0 && ms.id_slots == 0) {
+                uint32_t cnt = 0;
+                for (long long k = w; k < e; k++) cnt += __popc(P.arena[k]);
+                if (cnt) atomicAdd(&P.ms[m].n_set, cnt);
+            }
+            if (e > w) w = e;
+            m++;
+        }
     }
 }
 
@@ -603,6 +648,7 @@ __global__ void k_finalize(Params P)
     }
     ModState &s = P.ms[m];
     if (P.out && P.recompute_bound && s.hdr == S_OK) P.out[P.mod_off[m] + 3] = s.max_rid + 1;
+    if (P.validate && s.arena_off >= 0 && s.id_slots == 0 && s.n_set < s.n_ids) s.flags |= MF_DUP;
     if (P.validate && s.hdr == S_OK && !(s.flags & (MF_CAPACITY | MF_TIMEOUT)) && !P.ctrl->timeout) {
         uint64_t decl = ((uint64_t)s.decl_hi << 32) | s.decl_lo;
         uint64_t req = ((uint64_t)s.req_hi << 32) | s.req_lo;
@@ -762,8 +808,14 @@ __global__ void k_validate_rows(Params P)
         Walk wk = walk_instruction(iw, wc, d, ms->bound);
         if (!wk.ok) { atomicMin(&ms->err_key, make_key((unsigned long long)row, R_BADOP, 0)); continue; }
         if (wk.oob) { atomicMin(&ms->err_key, make_key((unsigned long long)row, R_OOB, 0)); continue; }
-        if ((d.flags & 4) && ms->arena_off >= 0 && idset_insert(P.arena + ms->arena_off, ms->id_slots, ri))
-            atomicOr(&ms->flags, MF_DUP);
+        if ((d.flags & 4) && ms->arena_off >= 0) {
+            if (ms->id_slots == 0) {
+                atomicOr(&P.arena[ms->arena_off + (ri >> 5)], 1u << (ri & 31));
+                atomicAdd(&ms->n_ids, 1u);
+            } else if (idset_insert(P.arena + ms->arena_off, ms->id_slots, ri)) {
+                atomicOr(&ms->flags, MF_DUP);
+            }
+        }
         uint64_t req = wk.req | width_caps(iw, op, wc);
         if ((uint32_t)req) atomicOr(&ms->req_lo, (uint32_t)req);
         if ((uint32_t)(req >> 32)) atomicOr(&ms->req_hi, (uint32_t)(req >> 32));
@@ -828,7 +880,7 @@ __global__ void k_encode_rows(const uint32_t *words, const int64_t *mod_off, con
 // host side
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t ctrl, tile_off, tile_mod, tstate, tmap, cstate, ms, fixlist, arena, total;
+    size_t ctrl, tile_off, tile_mod, tstate, tmap, cstate, ms, fixlist, abase, arena, total;
     long long max_tiles, arena_words;
 };
 
@@ -848,6 +900,7 @@ Layout make_layout(int n_mod, long long n_words, long long arena_words, int tile
     L.cstate = o; o = al(o + 8 * (size_t)L.max_tiles);
     L.ms = o; o = al(o + sizeof(ModState) * (size_t)n_mod);
     L.fixlist = o; o = al(o + 4 * (size_t)n_mod);
+    L.abase = o; o = al(o + 8 * (size_t)(n_mod + 1));
     L.arena = o; o = al(o + 4 * (size_t)L.arena_words);
     L.total = o;
     return L;
@@ -894,9 +947,16 @@ int launch_tile_kernel(const Params &P, int grid, cudaStream_t st)
 template <int NT, int L>
 int occupancy(int *per_sm)
 {
+    // computed once per device
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && cached[dev] > 0) { *per_sm = cached[dev]; return 0; }
     size_t sm = sizeof(TileSmem<NT, L>);
     cudaFuncSetAttribute(k_tile<NT, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tile<NT, L>, NT, sm) == cudaSuccess ? 0 : SPV_E_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tile<NT, L>, NT, sm) != cudaSuccess) return SPV_E_CUDA;
+    if (dev < 64) cached[dev] = *per_sm;
+    return 0;
 }
 
 int dispatch_tile(const Params &P, const Cfg &c, int grid, cudaStream_t st)
@@ -935,6 +995,7 @@ Params base_params(const spv_batch *b, void *ws, const Layout &L)
     P.cstate = (unsigned long long *)(w + L.cstate);
     P.ms = (ModState *)(w + L.ms);
     P.fixlist = (uint32_t *)(w + L.fixlist);
+    P.abase = (int64_t *)(w + L.abase);
     P.arena = (uint32_t *)(w + L.arena);
     P.arena_words = L.arena_words;
     return P;
@@ -942,10 +1003,14 @@ Params base_params(const spv_batch *b, void *ws, const Layout &L)
 
 int sm_count()
 {
+    static int cached[64] = {};
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
+    if (dev < 64 && cached[dev] > 0) return cached[dev];
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n > 0 ? n : 1;
+    if (n <= 0) n = 1;
+    if (dev < 64) cached[dev] = n;
+    return n;
 }
 
 }  // namespace
@@ -1008,6 +1073,7 @@ extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint3
     }
     if (rc) return rc;
     int nb = (batch->n_modules + 255) / 256;
+    if (validate) SPV_LAUNCH("k_id_popcount", st, k_id_popcount<<<nsm * 4, 256, 0, st>>>(P));
     SPV_LAUNCH("k_finalize", st, k_finalize<<<nb, 256, 0, st>>>(P));
     if (validate) SPV_LAUNCH("k_fixup", st, k_fixup<<<64, FIX_NT, 0, st>>>(P));
     return cudaPeekAtLastError() == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;
@@ -1048,6 +1114,7 @@ extern "C" int spv_validate_batch(const spv_batch *batch, const spv_table *table
     SPV_LAUNCH("k_tile_setup", st, k_tile_setup<<<nsm * 4, 256, 0, st>>>(P));
     SPV_LAUNCH("k_table_framing", st, k_table_framing<<<nb, 256, 0, st>>>(P));
     SPV_LAUNCH("k_validate_rows", st, k_validate_rows<<<nsm * 8, 256, 0, st>>>(P));
+    SPV_LAUNCH("k_id_popcount", st, k_id_popcount<<<nsm * 4, 256, 0, st>>>(P));
     SPV_LAUNCH("k_finalize", st, k_finalize<<<nb, 256, 0, st>>>(P));
     SPV_LAUNCH("k_fixup", st, k_fixup<<<64, FIX_NT, 0, st>>>(P));
     return cudaPeekAtLastError() == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;

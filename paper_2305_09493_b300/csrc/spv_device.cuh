@@ -64,6 +64,8 @@ struct ModState {                    // one per module
     uint32_t flags;
     long long arena_off;             // first word of this module's id set, -1 none
     uint32_t id_slots;               // 0: bitmap of ceil(bound / 32) words; else hash set of this many keys
+    uint32_t n_ids;                  // result ids inserted into a bitmap id set
+    uint32_t n_set;                  // bits set in the bitmap afterwards (fewer than n_ids: a duplicate)
     uint32_t pad2;
 };
 
@@ -231,18 +233,19 @@ __device__ Walk walk_instruction(const WordFn &word, uint32_t wc, const spvt::Op
         else if (c >= spvt::A_ENUM && c < spvt::A_ENUM + spvt::NUM_VKINDS) {
             int kind = c - spvt::A_ENUM;
             uint32_t v = word(pos++);
-            uint8_t params[3];
+            // the enumerant's parameter codes, packed in one register
+            uint32_t packed = 0;
             int np = 0;
             if (v < 64 && T.venum[kind][v].known) {
                 const spvt::EnDesc &e = T.venum[kind][v];
                 if (e.cap >= 0) r.req |= 1ull << e.cap;
                 np = e.nparam;
-                for (int q = 0; q < np; q++) params[q] = e.param[q];
+                packed = (uint32_t)e.param[0] | ((uint32_t)e.param[1] << 8) | ((uint32_t)e.param[2] << 16);
             } else if (T.vunknown[kind]) {
-                params[0] = T.vunknown[kind]; np = 1;
+                packed = T.vunknown[kind]; np = 1;
             }
             for (int q = 0; q < np && r.ok; q++) {
-                uint8_t pc = params[q];
+                uint8_t pc = (uint8_t)(packed >> (8 * q));
                 if (pc == spvt::A_LITS) { pos = wc; continue; }
                 if (pos >= wc) { r.ok = false; break; }
                 if (pc == spvt::A_ID) { SPV_ID_AT(pos); pos++; }

@@ -758,17 +758,22 @@ __global__ void __launch_bounds__(DNT) k_dis_main(DP P)
         }
         __syncthreads();
         // copy out: global words wholly inside the tile's byte range are
-        // stored whole; the partial words at either end byte by byte
+        // stored whole, each assembled from two aligned shared words (the
+        // shift between shared and global alignment is the same for the whole
+        // tile); the partial words at either end byte by byte
         if (write && staged && total) {
             const unsigned long long g0 = base, g1 = base + total;
             const unsigned long long w0 = g0 >> 2, w1 = (g1 + 3) >> 2;
             const bool aligned = (((uintptr_t)P.text) & 3) == 0;
+            const uint32_t sh = (uint32_t)(g0 & 3);          // global word w starts at shared byte 4(w - w0) - sh
+            const uint32_t *sw = reinterpret_cast<const uint32_t *>(s.text);
             uint32_t *tw = reinterpret_cast<uint32_t *>(P.text);
             for (unsigned long long w = w0 + tid; w < w1; w += DNT) {
                 unsigned long long gb = w << 2;
                 if (aligned && gb >= g0 && gb + 4 <= g1) {
-                    const unsigned char *src = reinterpret_cast<const unsigned char *>(s.text) + (gb - g0);
-                    tw[w] = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16) | ((uint32_t)src[3] << 24);
+                    uint32_t k = (uint32_t)(w - w0);           // >= 1 when sh != 0 (the first word is partial)
+                    uint32_t v = sh == 0 ? sw[k] : __funnelshift_r(sw[k - 1], sw[k], 8 * (4 - sh));
+                    tw[w] = v;
                 } else {
                     for (int b = 0; b < 4; b++) {
                         unsigned long long g = gb + b;
@@ -839,21 +844,22 @@ extern "C" int spv_disassemble_batch(const spv_batch *batch, const spv_table *ta
     P.tstate = (unsigned long long *)(w + L.tstate);
     P.arena = (uint32_t *)(w + L.arena); P.arena_words = L.arena_words;
     P.max_spins = 1LL << 20;
-    int dev = 0, nsm = 0;
+    // device properties and occupancy, once per device
+    static int cached_nsm[64] = {}, cached_per_sm[64] = {};
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 1;
-    static bool configured[64] = {};
-    if (dev < 64 && !configured[dev]) {
+    int nsm = dev < 64 ? cached_nsm[dev] : 0, per_sm = dev < 64 ? cached_per_sm[dev] : 0;
+    if (nsm <= 0 || per_sm <= 0) {
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 1;
         if (cudaFuncSetAttribute(k_dis_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MainSmem)) !=
             cudaSuccess)
             return SPV_E_CUDA;
-        configured[dev] = true;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dis_main, DNT, sizeof(MainSmem)) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        if (dev < 64) { cached_nsm[dev] = nsm; cached_per_sm[dev] = per_sm; }
     }
-    int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dis_main, DNT, sizeof(MainSmem)) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
     int nb = (batch->n_modules + 255) / 256;
     SPV_LAUNCH("k_dis_prepass", st, k_dis_prepass<<<1, 1024, 0, st>>>(P));
     SPV_LAUNCH("k_dis_clear", st, k_dis_clear<<<nsm * 4, 256, 0, st>>>(P));

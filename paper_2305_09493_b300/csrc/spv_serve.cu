@@ -182,8 +182,9 @@ void finish_requests(spv_server *s, Batch *b)
     s->done_cv.notify_all();
 }
 
-// launch a batch on a free slot; returns false when memory is short
-bool launch(spv_server *s, int slot)
+// launch a batch on a free slot; returns false when memory is short. The
+// server lock is held for the bookkeeping and released for the CUDA calls.
+bool launch(spv_server *s, int slot, std::unique_lock<std::mutex> &lk)
 {
     std::vector<Req *> take;
     int64_t words = 0;
@@ -238,6 +239,8 @@ bool launch(spv_server *s, int slot)
     int64_t o = 0;
     for (int i = 0; i < n; i++) { b->h_modoff[i] = o; take[i]->batch = b; take[i]->index = i; take[i]->state = 1; o += take[i]->n_words; }
     b->h_modoff[n] = o;
+    s->slot_busy[slot] = true;
+    lk.unlock();
     int rc = cudaSuccess;
     int i = 0;
     while (i < n && rc == cudaSuccess) {
@@ -272,8 +275,8 @@ bool launch(spv_server *s, int slot)
         cudaMemcpyAsync(b->h_ninstr, b->d_ninstr, 4 * (size_t)n, cudaMemcpyDeviceToHost, st);
         if (cudaLaunchHostFunc(st, on_stage, b) != cudaSuccess) e = SPV_E_CUDA;
     }
+    lk.lock();
     b->phase = 1;
-    s->slot_busy[slot] = true;
     s->inflight.push_back(b);
     if (e != SPV_SUCCESS) {
         b->error = e;
@@ -349,7 +352,7 @@ void scheduler(spv_server *s)
         if (s->stop && s->queue.empty() && s->inflight.empty()) break;
         bool launched = false;
         for (int slot = 0; slot < 2 && !s->queue.empty(); slot++)
-            if (!s->slot_busy[slot]) launched |= launch(s, slot);
+            if (!s->slot_busy[slot]) launched |= launch(s, slot, lk);
         if (!launched) s->cv.wait_for(lk, std::chrono::microseconds(50));
     }
 }
