@@ -104,7 +104,8 @@ typedef struct spv_table {
 /* Tuning of the batched kernels; zero fields take defaults. */
 typedef struct spv_config {
     int32_t tile_words;         /* words per tile: 1024, 2048, 4096 or 8192 (default 4096) */
-    int32_t threads;            /* threads per CTA: 128 or 256 (default 256); tile_words/threads must be 8 or 16 */
+    int32_t threads;            /* threads per CTA: 128, 256 or 512 (default 256); tile_words/threads must be 8
+                                   or 16, and 512 threads only with 16 */
     int32_t ctas_per_sm;        /* resident CTAs per SM for the persistent grid (default: occupancy maximum) */
     int32_t per_module;         /* 1: one launch sequence per module instead of one persistent launch
                                    (comparison path; copies mod_off to the host and synchronises) */

@@ -920,7 +920,7 @@ int resolve_cfg(const spv_config *c, Cfg *out)
         if (c->max_spins) r.max_spins = c->max_spins;
         r.stall_tile = c->test_stall_tile - 1;
     }
-    if (r.NT != 128 && r.NT != 256) return SPV_E_ARG;
+    if (r.NT != 128 && r.NT != 256 && r.NT != 512) return SPV_E_ARG;
     if (r.T % r.NT) return SPV_E_ARG;
     r.L = r.T / r.NT;
     if (r.L != 8 && r.L != 16) return SPV_E_ARG;
@@ -961,6 +961,7 @@ int occupancy(int *per_sm)
 
 int dispatch_tile(const Params &P, const Cfg &c, int grid, cudaStream_t st)
 {
+    if (c.NT == 512 && c.L == 16) return launch_tile_kernel<512, 16>(P, grid, st);
     if (c.NT == 256 && c.L == 16) return launch_tile_kernel<256, 16>(P, grid, st);
     if (c.NT == 256 && c.L == 8) return launch_tile_kernel<256, 8>(P, grid, st);
     if (c.NT == 128 && c.L == 16) return launch_tile_kernel<128, 16>(P, grid, st);
@@ -970,6 +971,7 @@ int dispatch_tile(const Params &P, const Cfg &c, int grid, cudaStream_t st)
 
 int dispatch_occupancy(const Cfg &c, int *per_sm)
 {
+    if (c.NT == 512 && c.L == 16) return occupancy<512, 16>(per_sm);
     if (c.NT == 256 && c.L == 16) return occupancy<256, 16>(per_sm);
     if (c.NT == 256 && c.L == 8) return occupancy<256, 8>(per_sm);
     if (c.NT == 128 && c.L == 16) return occupancy<128, 16>(per_sm);

@@ -360,3 +360,45 @@ def test_every_opcode_word_counts_and_operands(gpu):
                 mods.append(H.module(b, bound=50))
     words, offs = H.batch(mods)
     check(gpu, words, offs, dis=True)
+
+
+def _long_instruction_module(seed, n):
+    """A valid module whose instructions include many longer than 32 words
+    (wide struct types, phis with many pairs, long strings and names, calls
+    with many arguments), so that entries deep inside tiles and warp
+    segments occur."""
+    rng = np.random.default_rng(seed)
+    base = H.minimal_body()
+    head, tail = base[:7], base[7:]
+    body = list(head)
+    nid = 100
+    for k in range(n):
+        kind = int(rng.integers(0, 5))
+        if kind == 0:
+            body.append(H.ins(30, nid, [2] * int(rng.integers(1, 120))))                 # OpTypeStruct
+        elif kind == 1:
+            body.append(H.ins(H.OpString, nid, H.s("x" * int(rng.integers(1, 400)))))
+        elif kind == 2:
+            body.append(H.ins(H.OpName, 5, H.s("n" * int(rng.integers(1, 300)))))
+        elif kind == 3:
+            body.append(H.ins(H.OpTypeInt, nid, 32, 0))
+        else:
+            body.append(H.ins(44, 2, nid, [4] * int(rng.integers(1, 90))))               # OpConstantComposite
+        nid += 1
+    body.extend(tail)
+    return H.module(body, bound=nid + 1)
+
+
+@pytest.mark.parametrize("tile,threads", [(8192, 512), (4096, 256), (2048, 256), (2048, 128), (1024, 128)])
+def test_long_instructions_cross_tiles(gpu, tile, threads):
+    mods = [_long_instruction_module(s, 400) for s in range(3)]
+    words, offs = H.batch(mods)
+    st, er = oracle.validate(words, offs)
+    assert (st == 0).all()
+    check(gpu, words, offs, cfg=gpu.make_config(tile_words=tile, threads=threads), dis=(tile == 4096))
+
+
+def test_big_tiles_on_generated_batch(gpu):
+    n_instr, n_k = synth.batch_shape(80, 23, median=3000, lo=200, hi=40000)
+    w, off = synth.batch(n_instr, n_k, 23)
+    check(gpu, w, off, cfg=gpu.make_config(tile_words=8192, threads=512))
