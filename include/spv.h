@@ -212,9 +212,10 @@ typedef struct spv_dis_opts {
 
 /* Workspace bytes for spv_disassemble_batch. arena_words is the capacity,
  * in 32-bit words, of the per-module id tables (first OpName and first
- * definition of each id): 2 * bound words when bound <= 2 * len + 64, else a
- * hash map of 3 * (len + 64) words. 0 selects the default
- * 4 * n_words + 192 * n_modules + 64, which always fits every module. */
+ * definition of each id): 3 * bound words plus a bitmap of ceil(bound / 32)
+ * words when bound <= len + 64 (len = the module's words), else a hash map of
+ * 4 * (len + 64) words. 0 selects the default 4 * n_words + 256 * n_modules
+ * + 64, which always fits every module. */
 size_t spv_dis_workspace_bytes(int32_t n_modules, int64_t n_words, int64_t n_rows_capacity, int64_t arena_words);
 
 /*

@@ -30,10 +30,24 @@ using namespace spvd;
 namespace {
 
 constexpr uint32_t NOROW = 0xFFFFFFFFu;
-constexpr int DNT = 256;                 // threads per CTA
-constexpr int IPT = 2;                   // items per thread
-constexpr int ITEMS = DNT * IPT;         // items per tile
-constexpr int TEXT_SMEM = 40 * 1024;     // shared text buffer per tile
+#ifndef SPV_DIS_NT
+#define SPV_DIS_NT 256
+#endif
+#ifndef SPV_DIS_IPT
+#define SPV_DIS_IPT 2
+#endif
+#ifndef SPV_DIS_TEXT_KB
+#define SPV_DIS_TEXT_KB 40
+#endif
+#ifndef SPV_DIS_MIN_BLOCKS
+#define SPV_DIS_MIN_BLOCKS 1
+#endif
+constexpr int DNT = SPV_DIS_NT;                   // threads per CTA
+constexpr int IPT = SPV_DIS_IPT;                  // items per thread
+constexpr int ITEMS = DNT * IPT;                  // items per tile
+constexpr int TEXT_SMEM = SPV_DIS_TEXT_KB * 1024; // shared text buffer per tile
+constexpr int STAGE_WORDS = 4096;                 // a tile's instruction words staged in shared memory
+constexpr uint32_t NOSTAGE = 0xFFFFFFFFu;
 constexpr unsigned long long F_AGG = 1ull << 62, F_INC = 2ull << 62, F_MSK = 3ull << 62;
 
 struct DisCtrl {
@@ -66,6 +80,7 @@ struct DP {
     char *text; unsigned long long text_cap; uint64_t *text_off; uint32_t *dis_status;
     DisCtrl *ctrl; DisMod *dm; uint32_t *arena; long long arena_words;
     unsigned long long *tstate;
+    int *tile_m0;            // per tile of k_dis_main: the module holding its first item
     long long max_spins;
 };
 
@@ -83,7 +98,9 @@ __host__ __device__ inline bool idtab_dense(uint32_t bound, long long len)
 }
 __host__ __device__ inline unsigned long long idtab_words(uint32_t bound, long long len)
 {
-    return idtab_dense(bound, len) ? 3ull * bound : 4ull * ((unsigned long long)len + 64);
+    // dense: the table, then a bitmap with one bit per id, cleared when the id is named
+    return idtab_dense(bound, len) ? 3ull * bound + ((unsigned long long)bound + 31) / 32
+                                   : 4ull * ((unsigned long long)len + 64);
 }
 // the id's [name row, name length, def row] triple, or null when absent
 __device__ __forceinline__ uint32_t *idtab_entry(uint32_t *base, uint32_t bound, uint32_t slots, uint32_t id,
@@ -225,11 +242,14 @@ __device__ unsigned long long f32_to_f64_bits(uint32_t f)
 // per-row formatting
 // ---------------------------------------------------------------------------
 struct RowCtx {
-    const uint32_t *iw;          // the instruction's words
+    const uint32_t *iw;          // the instruction's words (shared or global memory)
     uint32_t wc, op;
     const DisMod *md;
     uint32_t *tab;               // the module's id table
-    const DP *P;
+    const uint32_t *words;       // the batch's words and table columns (values,
+    const uint64_t *off;         // not a pointer to the kernel's parameters,
+    const uint16_t *opcol;       // which would copy them to local memory)
+    bool inline_names;
     int64_t first;               // module's first row
     bool walk_ok;
 };
@@ -237,7 +257,11 @@ struct RowCtx {
 template <class Sink> __device__ void put_id(Sink &k, const RowCtx &c, uint32_t id)
 {
     k.put('%');
-    if (c.P->inline_names && id < c.md->bound) {
+    // dense tables keep a bitmap after the table whose bit is cleared for a
+    // named id: most ids have no name and cost one cached bit test
+    bool maybe_named = c.inline_names && id < c.md->bound &&
+                       (c.md->slots || !((c.tab[3ull * c.md->bound + (id >> 5)] >> (id & 31)) & 1u));
+    if (maybe_named) {
         const uint32_t *e = idtab_entry(c.tab, c.md->bound, c.md->slots, id, false);
         uint32_t nr = e ? e[0] : NOROW;
         if (nr != NOROW) {
@@ -245,7 +269,7 @@ template <class Sink> __device__ void put_id(Sink &k, const RowCtx &c, uint32_t 
                 k.n += e[1] + 1;
             } else {
                 int64_t row = c.first + nr;
-                const uint32_t *nw = c.P->words + c.P->off[row];
+                const uint32_t *nw = c.words + c.off[row];
                 uint32_t left = e[1];
                 for (uint32_t i = 2; left; i++) {
                     uint32_t v = __ldg(nw + i);
@@ -266,7 +290,7 @@ template <class Sink> __device__ __noinline__ Sink put_string(Sink k, const uint
 {
     k.put('"');
     for (uint32_t i = 0; i < n; i++) {
-        uint32_t v = __ldg(iw + pos + i);
+        uint32_t v = iw[pos + i];
         for (int b = 0; b < 4; b++) {
             unsigned ch = (v >> (8 * b)) & 0xffu;
             if (!ch) { k.put('"'); return k; }
@@ -310,7 +334,7 @@ template <class Sink> __device__ __noinline__ Sink put_raw_tail(Sink k, const ui
     if constexpr (Sink::counting) {
         k.n += 11 * (wc - 1);
     } else {
-        for (uint32_t i = 1; i < wc; i++) { k.put(' '); put_hex8(k, __ldg(iw + i)); }
+        for (uint32_t i = 1; i < wc; i++) { k.put(' '); put_hex8(k, iw[i]); }
     }
     return k;
 }
@@ -318,7 +342,7 @@ template <class Sink> __device__ __noinline__ Sink put_raw_tail(Sink k, const ui
 // one operand of a parameter list (no optional / repeat forms except A_LITS)
 template <class Sink> __device__ void put_param(Sink &k, const RowCtx &c, uint8_t pc, uint32_t &pos)
 {
-    auto word = [&](uint32_t i) -> uint32_t { return __ldg(c.iw + i); };
+    auto word = [&](uint32_t i) -> uint32_t { return c.iw[i]; };
     if (pc == spvt::A_LITS) { for (; pos < c.wc; pos++) { k.put(' '); put_dec(k, word(pos)); } return; }
     k.put(' ');
     if (pc == spvt::A_ID) { put_id(k, c, word(pos)); pos++; }
@@ -329,13 +353,13 @@ template <class Sink> __device__ void put_param(Sink &k, const RowCtx &c, uint8_
 
 template <class Sink> __device__ __noinline__ Sink put_ctx_literal(Sink k, RowCtx c, uint32_t rt, uint32_t pos)
 {
-    auto word = [&](uint32_t i) -> uint32_t { return __ldg(c.iw + i); };
+    auto word = [&](uint32_t i) -> uint32_t { return c.iw[i]; };
     uint32_t n = c.wc - pos;
     bool is_float = false;
     if (rt < c.md->bound) {
         const uint32_t *e = idtab_entry(c.tab, c.md->bound, c.md->slots, rt, false);
         uint32_t dr = e ? e[2] : NOROW;
-        if (dr != NOROW && c.P->op[c.first + dr] == 22) is_float = true;
+        if (dr != NOROW && c.opcol[c.first + dr] == 22) is_float = true;
     }
     k.put(' ');
     if (is_float && n == 1) k = put_hexfloat64(k, f32_to_f64_bits(word(pos)));
@@ -349,7 +373,7 @@ template <class Sink> __device__ __noinline__ Sink put_ctx_literal(Sink k, RowCt
 template <class Sink> __device__ void format_row(Sink &k, const RowCtx &c)
 {
     const spvt::Tables &T = g_spv_tables;
-    auto word = [&](uint32_t i) -> uint32_t { return __ldg(c.iw + i); };
+    auto word = [&](uint32_t i) -> uint32_t { return c.iw[i]; };
     if (c.op >= 256 || !(T.ops[c.op].flags & 1)) {
         k.put('O'); k.put('p'); put_dec(k, c.op);
         k = put_raw_tail(k, c.iw, c.wc); k.put('\n');
@@ -489,13 +513,22 @@ __global__ void __launch_bounds__(1024) k_dis_prepass(DP P)
     }
 }
 
+// id tables to NOROW (dense bitmaps to all ones: nothing named), look-back
+// states to zero, and the tile -> first module map: every module owns the
+// tiles whose first item falls in its item range
 __global__ void k_dis_clear(DP P)
 {
     unsigned long long n = P.ctrl->arena_used;
-    unsigned long long nt = P.ctrl->n_items / ITEMS + 1;
+    const long long n_items = (long long)P.ctrl->n_items;
+    unsigned long long nt = n_items / ITEMS + 1;
     long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)n; i += stride) P.arena[i] = NOROW;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)nt; i += stride) P.tstate[i] = 0;
+    long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long i = g; i < (long long)n; i += stride) P.arena[i] = NOROW;
+    for (long long i = g; i < (long long)nt; i += stride) P.tstate[i] = 0;
+    for (long long m = g; m < P.n_mod; m += stride) {
+        long long b = P.dm[m].item_base, e = m + 1 < P.n_mod ? P.dm[m + 1].item_base : n_items;
+        for (long long t = (b + ITEMS - 1) / ITEMS; t * ITEMS < e; t++) P.tile_m0[t] = (int)m;
+    }
 }
 
 // first OpName per id and first definition per id (module-local rows)
@@ -513,7 +546,10 @@ __global__ void k_dis_ids(DP P)
         uint32_t *tab = P.arena + md.arena_off;
         if (op == 5 && wc >= 2 && P.inline_names) {
             uint32_t target = __ldg(P.words + P.off[row] + 1);
-            if (target < md.bound) atomicMin(&idtab_entry(tab, md.bound, md.slots, target, true)[0], local);
+            if (target < md.bound) {
+                atomicMin(&idtab_entry(tab, md.bound, md.slots, target, true)[0], local);
+                if (!md.slots) atomicAnd(&tab[3ull * md.bound + (target >> 5)], ~(1u << (target & 31)));
+            }
         }
         if (op < 256 && (T.ops[op].flags & 4)) {
             uint32_t q = 1 + ((T.ops[op].flags >> 1) & 1);
@@ -566,8 +602,12 @@ struct MainSmem {
     uint32_t ioff[ITEMS];           // per item: offset in the tile's text
     uint16_t perm[ITEMS];           // items grouped by text shape
     uint16_t rank[ITEMS];           // per item: position within its shape group
+    uint32_t irel[ITEMS];           // per item: its words at wst[irel], NOSTAGE when not staged
+    uint16_t iop[ITEMS], iwc[ITEMS];// per item: opcode and word count
     uint8_t icls[ITEMS];            // per item: shape class
     uint8_t iok[ITEMS];             // per item: operands parse (else raw words)
+    uint32_t wst[STAGE_WORDS];      // words [wlo, wlo + STAGE_WORDS) of the batch
+    unsigned long long wlo, whi;
     uint32_t cls_n[NSHAPE];
     uint32_t warp_tot[DNT / 32];
     long long tile;
@@ -576,51 +616,102 @@ struct MainSmem {
     int gave_up;
 };
 
-__device__ __forceinline__ bool make_ctx(const DP &P, int m, long long row, RowCtx &c, int walk_ok)
+__device__ __forceinline__ bool make_ctx(const DP &P, const MainSmem &s, int j, int m, long long row, RowCtx &c,
+                                         int walk_ok)
 {
     const DisMod &md = P.dm[m];
     if (!md.ok) return false;
-    c.iw = P.words + P.off[row];
-    c.wc = P.wc[row];
-    c.op = P.op[row];
+    c.iw = s.irel[j] != NOSTAGE ? s.wst + s.irel[j] : P.words + P.off[row];
+    c.wc = s.iwc[j];
+    c.op = s.iop[j];
     c.md = &md;
     c.tab = P.arena + md.arena_off;
-    c.P = &P;
+    c.words = P.words;
+    c.off = P.off;
+    c.opcol = P.op;
+    c.inline_names = P.inline_names != 0;
     c.first = P.first_row[m];
     if (walk_ok >= 0) c.walk_ok = walk_ok != 0;
     else {
         c.walk_ok = true;
         if (c.op < 256 && (g_spv_tables.ops[c.op].flags & 1)) {
-            auto word = [&](uint32_t i) -> uint32_t { return __ldg(c.iw + i); };
+            auto word = [&](uint32_t i) -> uint32_t { return c.iw[i]; };
             c.walk_ok = walk_instruction(word, c.wc, g_spv_tables.ops[c.op], 0xffffffffu).ok;
         }
     }
     return true;
 }
 
+// Warp 0: tile t's text offset, the sum of all earlier tiles' byte counts
+// (decoupled look-back over the published aggregates / inclusive prefixes).
+// Publishes tile t's inclusive prefix; a wait that runs out sets the timeout
+// flag and leaves s.gave_up set.
+__device__ void dis_lookback(const DP &P, MainSmem &s, long long t, uint32_t total, int lane, bool last_tile)
+{
+    unsigned long long excl = 0;
+    if (t > 0) {
+        long long hi = t - 1, spins = 0;
+        bool gave_up = false;
+        for (;;) {
+            long long jj = hi - lane;
+            unsigned long long st = jj >= 0 ? ld_acquire(&P.tstate[jj]) : F_INC;
+            unsigned long long f = st & F_MSK;
+            unsigned incm = __ballot_sync(0xffffffffu, f == F_INC);
+            unsigned nonem = __ballot_sync(0xffffffffu, f == 0);
+            int le = incm ? __ffs(incm) - 1 : 32;
+            unsigned below = le == 32 ? 0xffffffffu : ((1u << le) - 1u);
+            if (nonem & below) {
+                if (++spins > P.max_spins) { gave_up = true; break; }
+                spin_pause();
+                continue;
+            }
+            unsigned long long v2 = (lane <= le && jj >= 0) ? (st & ~F_MSK) : 0ull;
+            #pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, d);
+            excl += v2;
+            if (incm) break;
+            hi -= 32;
+        }
+        if (gave_up && lane == 0) { atomicExch(&P.ctrl->timeout, 1u); s.gave_up = 1; }
+        if (lane == 0) st_release(&P.tstate[t], F_INC | (excl + total));
+    }
+    if (lane == 0) {
+        s.base = excl;
+        if (last_tile) P.text_off[P.n_mod] = excl + total;
+    }
+}
+
 // One tile of items: locate, group by text shape (so the lines a warp
-// formats share their control flow), measure, scan, format, copy out.
-__global__ void __launch_bounds__(DNT) k_dis_main(DP P)
+// formats share their control flow), measure, scan, publish the tile's byte
+// count, format into shared memory, look back for the tile's offset, copy
+// out. Formatting before the look-back gives the earlier tiles time to
+// publish, so the look-back seldom waits.
+__global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MainSmem &s = *reinterpret_cast<MainSmem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n_items = (long long)P.ctrl->n_items;
     const long long ntiles = (n_items + ITEMS - 1) / ITEMS;
+    // tickets are taken one tile ahead; a ticket's holder is running, and a
+    // tile waits only on lower tiles, so the look-backs always end
+    unsigned int ticket = 0;
+    if (tid == 0) ticket = atomicAdd(&P.ctrl->next_tile, 1u);
     for (;;) {
         if (tid == 0) {
-            s.tile = (long long)atomicAdd(&P.ctrl->next_tile, 1u);
+            s.tile = (long long)ticket;
             s.gave_up = 0;
-            if (s.tile < ntiles) {
-                long long i0 = s.tile * ITEMS;
-                int lo = 0, hi = P.n_mod;            // last module whose header item is <= i0
-                while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (P.dm[mid].item_base <= i0) lo = mid; else hi = mid; }
-                s.m0 = lo;
-                int nm = P.n_mod - lo;
-                s.nm = nm < ITEMS + 1 ? nm : ITEMS + 1;
+            if ((long long)ticket < ntiles) {
+                long long tt = (long long)ticket;
+                ticket = atomicAdd(&P.ctrl->next_tile, 1u);
+                int m0 = P.tile_m0[tt];
+                int m1 = tt + 1 < ntiles ? P.tile_m0[tt + 1] : P.n_mod - 1;
+                s.m0 = m0;
+                s.nm = m1 - m0 + 1;                  // <= ITEMS + 1
             }
         }
         if (tid < NSHAPE) s.cls_n[tid] = 0;
+        if (tid == 0) { s.wlo = ~0ull; s.whi = 0; }
         __syncthreads();
         const long long t = s.tile;
         if (t >= ntiles) break;
@@ -630,25 +721,59 @@ __global__ void __launch_bounds__(DNT) k_dis_main(DP P)
             s.ibase[j] = j < nm ? P.dm[m0 + j].item_base : (m0 + nm < P.n_mod ? P.dm[m0 + nm].item_base : n_items);
         __syncthreads();
 
-        // 1. locate every item and count the shape classes
-        for (int j = tid; j < ITEMS; j += DNT) {
-            long long i = i0 + j;
-            int m = -1, cls = 0;
-            long long row = -1;
-            if (i < n_items) {
-                int lo = 0, hi = nm;                 // last k with ibase[k] <= i
-                while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (s.ibase[mid] <= i) lo = mid; else hi = mid; }
-                m = m0 + lo;
-                if (i != s.ibase[lo]) {
-                    row = P.first_row[m] + (i - s.ibase[lo] - 1);
-                    uint32_t op = P.op[row];
-                    cls = op < 256 ? g_spv_tables.shape[op] : 1;
+        // 1. locate every item (op, word count and word offset read once,
+        //    coalesced), count the shape classes, find the tile's word range
+        {
+            unsigned long long lo_w = ~0ull, hi_w = 0;
+            for (int j = tid; j < ITEMS; j += DNT) {
+                long long i = i0 + j;
+                int m = -1, cls = 0;
+                long long row = -1;
+                uint32_t op = 0, wc = 0;
+                if (i < n_items) {
+                    int lo = 0, hi = nm;                 // last k with ibase[k] <= i
+                    while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (s.ibase[mid] <= i) lo = mid; else hi = mid; }
+                    m = m0 + lo;
+                    if (i != s.ibase[lo]) {
+                        row = P.first_row[m] + (i - s.ibase[lo] - 1);
+                        op = P.op[row];
+                        wc = P.wc[row];
+                        unsigned long long o = P.off[row];
+                        lo_w = o < lo_w ? o : lo_w;
+                        hi_w = o + wc > hi_w ? o + wc : hi_w;
+                        cls = op < 256 ? g_spv_tables.shape[op] : 1;
+                    }
                 }
+                s.im[j] = m;
+                s.irow[j] = row;
+                s.iop[j] = (uint16_t)op;
+                s.iwc[j] = (uint16_t)wc;
+                s.icls[j] = (uint8_t)cls;
+                s.rank[j] = (uint16_t)atomicAdd(&s.cls_n[cls], 1u);
             }
-            s.im[j] = m;
-            s.irow[j] = row;
-            s.icls[j] = (uint8_t)cls;
-            s.rank[j] = (uint16_t)atomicAdd(&s.cls_n[cls], 1u);
+            #pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                unsigned long long a = __shfl_xor_sync(0xffffffffu, lo_w, d), b = __shfl_xor_sync(0xffffffffu, hi_w, d);
+                lo_w = a < lo_w ? a : lo_w;
+                hi_w = b > hi_w ? b : hi_w;
+            }
+            if (lane == 0 && hi_w) { atomicMin(&s.wlo, lo_w); atomicMax(&s.whi, hi_w); }
+        }
+        __syncthreads();
+        // stage the words [wlo, min(whi, wlo + STAGE_WORDS)); an item whose
+        // words all lie inside reads them from shared memory
+        {
+            const unsigned long long wlo = s.wlo, whi = s.whi;
+            const uint32_t wn = whi > wlo ? (uint32_t)(whi - wlo < STAGE_WORDS ? whi - wlo : STAGE_WORDS) : 0u;
+            for (uint32_t k = tid; k < wn; k += DNT) s.wst[k] = P.words[wlo + k];
+            for (int j = tid; j < ITEMS; j += DNT) {
+                uint32_t rel = NOSTAGE;
+                if (s.irow[j] >= 0) {
+                    unsigned long long o = P.off[s.irow[j]];
+                    if (o + s.iwc[j] <= wlo + wn) rel = (uint32_t)(o - wlo);
+                }
+                s.irel[j] = rel;
+            }
         }
         __syncthreads();
         if (wid == 0) {                               // exclusive scan of the class counts
@@ -677,17 +802,19 @@ __global__ void __launch_bounds__(DNT) k_dis_main(DP P)
                 if (s.irow[j] < 0) len = P.dm[m].header_len;
                 else {
                     RowCtx c;
-                    if (make_ctx(P, m, s.irow[j], c, -1)) { CountSink k; format_row(k, c); len = k.n; ok = c.walk_ok; }
+                    if (make_ctx(P, s, j, m, s.irow[j], c, -1)) { CountSink k; format_row(k, c); len = k.n; ok = c.walk_ok; }
                 }
             }
             s.ilen[j] = len;
             s.iok[j] = ok;
         }
         __syncthreads();
-        // 3. scan in item order (two consecutive items per thread), then the tile's base
+        // 3. scan in item order (IPT consecutive items per thread)
         {
-            uint32_t a = s.ilen[2 * tid], b = s.ilen[2 * tid + 1];
-            uint32_t mine = a + b, incl = mine;
+            uint32_t mine = 0;
+            #pragma unroll
+            for (int q = 0; q < IPT; q++) mine += s.ilen[IPT * tid + q];
+            uint32_t incl = mine;
             #pragma unroll
             for (int d = 1; d < 32; d <<= 1) { uint32_t v = __shfl_up_sync(0xffffffffu, incl, d); if (lane >= d) incl += v; }
             if (lane == 31) s.warp_tot[wid] = incl;
@@ -696,67 +823,39 @@ __global__ void __launch_bounds__(DNT) k_dis_main(DP P)
             #pragma unroll
             for (int w = 0; w < DNT / 32; w++) if (w < wid) wpre += s.warp_tot[w];
             uint32_t ex = wpre + incl - mine;
-            s.ioff[2 * tid] = ex;
-            s.ioff[2 * tid + 1] = ex + a;
+            #pragma unroll
+            for (int q = 0; q < IPT; q++) { s.ioff[IPT * tid + q] = ex; ex += s.ilen[IPT * tid + q]; }
         }
         uint32_t total = 0;
         #pragma unroll
         for (int w = 0; w < DNT / 32; w++) total += s.warp_tot[w];
-        if (wid == 0) {
-            unsigned long long excl = 0;
-            if (t == 0) {
-                if (lane == 0) st_release(&P.tstate[0], F_INC | total);
-            } else {
-                if (lane == 0) st_release(&P.tstate[t], F_AGG | total);
-                long long hi = t - 1, spins = 0;
-                bool gave_up = false;
-                for (;;) {
-                    long long jj = hi - lane;
-                    unsigned long long st = jj >= 0 ? ld_acquire(&P.tstate[jj]) : F_INC;
-                    unsigned long long f = st & F_MSK;
-                    unsigned incm = __ballot_sync(0xffffffffu, f == F_INC);
-                    unsigned nonem = __ballot_sync(0xffffffffu, f == 0);
-                    int le = incm ? __ffs(incm) - 1 : 32;
-                    unsigned below = le == 32 ? 0xffffffffu : ((1u << le) - 1u);
-                    if (nonem & below) {
-                        if (++spins > P.max_spins) { gave_up = true; break; }
-                        spin_pause();
-                        continue;
-                    }
-                    unsigned long long v2 = (lane <= le && jj >= 0) ? (st & ~F_MSK) : 0ull;
-                    #pragma unroll
-                    for (int d = 16; d > 0; d >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, d);
-                    excl += v2;
-                    if (incm) break;
-                    hi -= 32;
-                }
-                if (gave_up && lane == 0) { atomicExch(&P.ctrl->timeout, 1u); s.gave_up = 1; }
-                if (lane == 0) st_release(&P.tstate[t], F_INC | (excl + total));
+        // the tile's byte count, published before any wait of this tile
+        if (tid == 0) st_release(&P.tstate[t], (t == 0 ? F_INC : F_AGG) | total);
+        const bool last_tile = i0 + ITEMS >= n_items;
+        const bool staged = total <= (uint32_t)TEXT_SMEM;
+        if (!staged && wid == 0) dis_lookback(P, s, t, total, lane, last_tile);   // oversized tile: its offset first
+        __syncthreads();                              // every item's offset (and an oversized tile's base)
+        // 4. format once, in shape order (into shared memory, or straight to
+        //    global memory for oversized tiles)
+        if (staged ? P.text_cap > 0 : (!s.gave_up && s.base + total <= P.text_cap)) {
+            const unsigned long long gbase = staged ? 0 : s.base;
+            for (int q = tid; q < ITEMS; q += DNT) {
+                int j = s.perm[q];
+                if (s.im[j] < 0 || s.ilen[j] == 0) continue;
+                char *dst = staged ? s.text + s.ioff[j] : P.text + gbase + s.ioff[j];
+                WriteSink k{dst};
+                if (s.irow[j] < 0) format_header(k, P.words + P.mod_off[s.im[j]]);
+                else { RowCtx c; make_ctx(P, s, j, s.im[j], s.irow[j], c, s.iok[j]); format_row(k, c); }
             }
-            if (lane == 0) {
-                s.base = excl;
-                if (i0 + ITEMS >= n_items) P.text_off[P.n_mod] = excl + total;
-            }
+        }
+        if (staged) {
+            if (wid == 0) dis_lookback(P, s, t, total, lane, last_tile);
         }
         __syncthreads();
         const unsigned long long base = s.base;
         for (int j = tid; j < ITEMS; j += DNT)
             if (s.im[j] >= 0 && s.irow[j] < 0) P.text_off[s.im[j]] = base + s.ioff[j];
         const bool write = !s.gave_up && base + total <= P.text_cap;
-        const bool staged = total <= (uint32_t)TEXT_SMEM;
-        // 4. format once, in shape order (into shared memory, or straight to
-        //    global memory for oversized tiles)
-        if (write) {
-            for (int q = tid; q < ITEMS; q += DNT) {
-                int j = s.perm[q];
-                if (s.im[j] < 0 || s.ilen[j] == 0) continue;
-                char *dst = staged ? s.text + s.ioff[j] : P.text + base + s.ioff[j];
-                WriteSink k{dst};
-                if (s.irow[j] < 0) format_header(k, P.words + P.mod_off[s.im[j]]);
-                else { RowCtx c; make_ctx(P, s.im[j], s.irow[j], c, s.iok[j]); format_row(k, c); }
-            }
-        }
-        __syncthreads();
         // copy out: global words wholly inside the tile's byte range are
         // stored whole, each assembled from two aligned shared words (the
         // shift between shared and global alignment is the same for the whole
@@ -792,7 +891,7 @@ __global__ void k_dis_status(DP P)
     if (m < P.n_mod && P.dis_status) P.dis_status[m] = P.ctrl->timeout ? S_TIMEOUT : P.dm[m].status;
 }
 
-struct DLayout { size_t ctrl, dm, tstate, arena, total; long long arena_words; };
+struct DLayout { size_t ctrl, dm, tstate, tile_m0, arena, total; long long arena_words; };
 size_t dal(size_t x) { return (x + 255) & ~size_t(255); }
 DLayout dlayout(int n_mod, long long n_words, long long rows_cap, long long arena_words)
 {
@@ -802,6 +901,7 @@ DLayout dlayout(int n_mod, long long n_words, long long rows_cap, long long aren
     L.ctrl = o; o = dal(o + sizeof(DisCtrl));
     L.dm = o; o = dal(o + sizeof(DisMod) * (size_t)n_mod);
     L.tstate = o; o = dal(o + 8 * (size_t)((rows_cap + n_mod) / ITEMS + 2));
+    L.tile_m0 = o; o = dal(o + 4 * (size_t)((rows_cap + n_mod) / ITEMS + 2));
     L.arena = o; o = dal(o + 4 * (size_t)L.arena_words);
     L.total = o;
     return L;
@@ -842,6 +942,7 @@ extern "C" int spv_disassemble_batch(const spv_batch *batch, const spv_table *ta
     P.text = text; P.text_cap = text_capacity; P.text_off = text_off; P.dis_status = dis_status;
     P.ctrl = (DisCtrl *)(w + L.ctrl); P.dm = (DisMod *)(w + L.dm);
     P.tstate = (unsigned long long *)(w + L.tstate);
+    P.tile_m0 = (int *)(w + L.tile_m0);
     P.arena = (uint32_t *)(w + L.arena); P.arena_words = L.arena_words;
     P.max_spins = 1LL << 20;
     // device properties and occupancy, once per device
