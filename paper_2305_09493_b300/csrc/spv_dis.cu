@@ -31,13 +31,13 @@ namespace {
 
 constexpr uint32_t NOROW = 0xFFFFFFFFu;
 #ifndef SPV_DIS_NT
-#define SPV_DIS_NT 256
+#define SPV_DIS_NT 512
 #endif
 #ifndef SPV_DIS_IPT
-#define SPV_DIS_IPT 2
+#define SPV_DIS_IPT 4
 #endif
 #ifndef SPV_DIS_TEXT_KB
-#define SPV_DIS_TEXT_KB 40
+#define SPV_DIS_TEXT_KB 80
 #endif
 #ifndef SPV_DIS_MIN_BLOCKS
 #define SPV_DIS_MIN_BLOCKS 1
@@ -46,7 +46,10 @@ constexpr int DNT = SPV_DIS_NT;                   // threads per CTA
 constexpr int IPT = SPV_DIS_IPT;                  // items per thread
 constexpr int ITEMS = DNT * IPT;                  // items per tile
 constexpr int TEXT_SMEM = SPV_DIS_TEXT_KB * 1024; // shared text buffer per tile
-constexpr int STAGE_WORDS = 4096;                 // a tile's instruction words staged in shared memory
+#ifndef SPV_DIS_STAGE_WORDS
+#define SPV_DIS_STAGE_WORDS 10240
+#endif
+constexpr int STAGE_WORDS = SPV_DIS_STAGE_WORDS;  // a tile's instruction words staged in shared memory
 constexpr uint32_t NOSTAGE = 0xFFFFFFFFu;
 constexpr unsigned long long F_AGG = 1ull << 62, F_INC = 2ull << 62, F_MSK = 3ull << 62;
 
@@ -65,7 +68,7 @@ struct DisMod {
     uint32_t slots;          // 0: direct table by id (3 words per id); else hash map (4 words per slot)
     uint32_t header_len;     // bytes of the header comment lines (0 when not printed)
     uint32_t status;         // S_OK / header status / S_CAPACITY
-    uint32_t pad;
+    uint32_t named;          // 1 when some OpName names an id of the module
     long long item_base;     // index of the module's header item
 };
 
@@ -118,10 +121,15 @@ __device__ __forceinline__ uint32_t *idtab_entry(uint32_t *base, uint32_t bound,
 }
 
 // header comment lines: "; SPIR-V\n; Version: M.m\n; Generator: 0x%08x\n; Bound: B\n; Schema: S\n"
+static __device__ const uint32_t c_pow10[10] = {1u, 10u, 100u, 1000u, 10000u, 100000u, 1000000u, 10000000u,
+                                                 100000000u, 1000000000u};
+// decimal digits of v: with b its bit length, t = floor(b * 1233 / 4096)
+// (1233 / 4096 just below log10(2)) makes the count t + 1 when v >= 10^t, else t
 __device__ __forceinline__ uint32_t dec_len32(uint32_t v)
 {
-    return 1u + (v >= 10u) + (v >= 100u) + (v >= 1000u) + (v >= 10000u) + (v >= 100000u) + (v >= 1000000u) +
-           (v >= 10000000u) + (v >= 100000000u) + (v >= 1000000000u);
+    uint32_t u = v | 1u;                               // 0 prints like 1: one digit
+    uint32_t t = ((32u - __clz(u)) * 1233u) >> 12;
+    return t + 1u - (u < c_pow10[t] ? 1u : 0u);
 }
 __device__ __forceinline__ uint32_t dec_len64(unsigned long long v)
 {
@@ -141,16 +149,29 @@ __device__ uint32_t header_len(const uint32_t *w)
 // sinks: the formatter below runs once counting, once writing
 // ---------------------------------------------------------------------------
 struct CountSink {
-    static constexpr bool counting = true;
+    static constexpr bool counting = true, clipping = false;
     uint32_t n = 0;
     __device__ __forceinline__ void put(char) { n++; }
     __device__ __forceinline__ void puts(const char *, int len) { n += len; }
 };
 struct WriteSink {
-    static constexpr bool counting = false;
+    static constexpr bool counting = false, clipping = false;
     char *p;
     __device__ __forceinline__ void put(char c) { *p++ = c; }
     __device__ __forceinline__ void puts(const char *s, int len) { for (int i = 0; i < len; i++) p[i] = s[i]; p += len; }
+};
+// writes only the bytes of a window [0, lim) of positions; p starts at the
+// line's position relative to the window (possibly negative)
+struct ClipSink {
+    static constexpr bool counting = false, clipping = true;
+    char *buf;
+    long long p, lim;
+    __device__ __forceinline__ void put(char c)
+    {
+        if ((unsigned long long)p < (unsigned long long)lim) buf[p] = c;
+        p++;
+    }
+    __device__ __forceinline__ void puts(const char *s, int len) { for (int i = 0; i < len; i++) put(s[i]); }
 };
 
 template <class Sink> __device__ __forceinline__ void put_lit(Sink &k, const char *s)
@@ -159,10 +180,27 @@ template <class Sink> __device__ __forceinline__ void put_lit(Sink &k, const cha
     while (s[n]) n++;
     k.puts(s, n);
 }
+template <class Sink> __device__ __forceinline__ void put_dec(Sink &k, uint32_t v)
+{
+    if constexpr (Sink::counting) {
+        k.n += dec_len32(v);
+    } else if constexpr (Sink::clipping) {
+        for (int i = (int)dec_len32(v) - 1; i >= 0; i--) k.put((char)('0' + (v / c_pow10[i]) % 10u));
+    } else {
+        uint32_t n = dec_len32(v);
+        char *e = k.p + n;
+        do { *--e = (char)('0' + v % 10u); v /= 10u; } while (v);
+        k.p += n;
+    }
+}
 template <class Sink> __device__ __forceinline__ void put_dec(Sink &k, unsigned long long v)
 {
     if constexpr (Sink::counting) {
         k.n += dec_len64(v);
+    } else if constexpr (Sink::clipping) {
+        unsigned long long pw = 1;
+        for (uint32_t i = 1; i < dec_len64(v); i++) pw *= 10;
+        for (; pw; pw /= 10) k.put((char)('0' + (v / pw) % 10));
     } else {
         // digits written backwards into place: no local buffer
         uint32_t n = dec_len64(v);
@@ -230,9 +268,12 @@ __device__ unsigned long long f32_to_f64_bits(uint32_t f)
     if (e == 0xff) return s | (0x7ffull << 52) | ((unsigned long long)m << 29);
     if (e == 0) {
         if (m == 0) return s;
-        int lz = __clz(m) - 8;              // leading zeros within the 23-bit field (1..23)
-        m = (m << (lz + 1)) & 0x7fffff;      // normalise: drop the leading one
-        unsigned long long ex = (unsigned long long)(1023 - 126 - (lz + 1));
+        // value m * 2^-149 with the leading one of m at bit 31 - clz(m):
+        // shifting by lz = clz(m) - 8 (1..23) moves it to bit 23, where the
+        // mask drops it, and the value is 1.f * 2^(-126 - lz)
+        int lz = __clz(m) - 8;
+        m = (m << lz) & 0x7fffff;
+        unsigned long long ex = (unsigned long long)(1023 - 126 - lz);
         return s | (ex << 52) | ((unsigned long long)m << 29);
     }
     return s | ((unsigned long long)(e - 127 + 1023) << 52) | ((unsigned long long)m << 29);
@@ -244,7 +285,8 @@ __device__ unsigned long long f32_to_f64_bits(uint32_t f)
 struct RowCtx {
     const uint32_t *iw;          // the instruction's words (shared or global memory)
     uint32_t wc, op;
-    const DisMod *md;
+    uint32_t bound, slots;       // the module's bound and id-table form (values:
+    bool named;                  // byte stores through a sink cannot alias them)
     uint32_t *tab;               // the module's id table
     const uint32_t *words;       // the batch's words and table columns (values,
     const uint64_t *off;         // not a pointer to the kernel's parameters,
@@ -254,35 +296,41 @@ struct RowCtx {
     bool walk_ok;
 };
 
-template <class Sink> __device__ void put_id(Sink &k, const RowCtx &c, uint32_t id)
+// "<name>_" of a named id (nothing when the id has no name); kept out of
+// line: most ids have no name, and an inlined copy at every id operand of
+// both formatter passes bloats the kernel's code
+template <class Sink> __device__ __noinline__ Sink put_id_name(Sink k, RowCtx c, uint32_t id)
+{
+    const uint32_t *e = idtab_entry(c.tab, c.bound, c.slots, id, false);
+    uint32_t nr = e ? e[0] : NOROW;
+    if (nr == NOROW) return k;
+    if constexpr (Sink::counting) {
+        k.n += e[1] + 1;
+    } else {
+        int64_t row = c.first + nr;
+        const uint32_t *nw = c.words + c.off[row];
+        uint32_t left = e[1];
+        for (uint32_t i = 2; left; i++) {
+            uint32_t v = __ldg(nw + i);
+            for (int b = 0; b < 4 && left; b++, left--) {
+                unsigned ch = (v >> (8 * b)) & 0xffu;
+                bool keep = (ch >= '0' && ch <= '9') || (ch >= 'A' && ch <= 'Z') || (ch >= 'a' && ch <= 'z') || ch == '_';
+                k.put(keep ? (char)ch : '_');
+            }
+        }
+        k.put('_');
+    }
+    return k;
+}
+
+template <class Sink> __device__ __forceinline__ void put_id(Sink &k, const RowCtx &c, uint32_t id)
 {
     k.put('%');
     // dense tables keep a bitmap after the table whose bit is cleared for a
     // named id: most ids have no name and cost one cached bit test
-    bool maybe_named = c.inline_names && id < c.md->bound &&
-                       (c.md->slots || !((c.tab[3ull * c.md->bound + (id >> 5)] >> (id & 31)) & 1u));
-    if (maybe_named) {
-        const uint32_t *e = idtab_entry(c.tab, c.md->bound, c.md->slots, id, false);
-        uint32_t nr = e ? e[0] : NOROW;
-        if (nr != NOROW) {
-            if constexpr (Sink::counting) {
-                k.n += e[1] + 1;
-            } else {
-                int64_t row = c.first + nr;
-                const uint32_t *nw = c.words + c.off[row];
-                uint32_t left = e[1];
-                for (uint32_t i = 2; left; i++) {
-                    uint32_t v = __ldg(nw + i);
-                    for (int b = 0; b < 4 && left; b++, left--) {
-                        unsigned ch = (v >> (8 * b)) & 0xffu;
-                        bool keep = (ch >= '0' && ch <= '9') || (ch >= 'A' && ch <= 'Z') || (ch >= 'a' && ch <= 'z') || ch == '_';
-                        k.put(keep ? (char)ch : '_');
-                    }
-                }
-                k.put('_');
-            }
-        }
-    }
+    if (c.named && id < c.bound &&
+        (c.slots || !((c.tab[3ull * c.bound + (id >> 5)] >> (id & 31)) & 1u)))
+        k = put_id_name(k, c, id);
     put_dec(k, id);
 }
 
@@ -356,8 +404,8 @@ template <class Sink> __device__ __noinline__ Sink put_ctx_literal(Sink k, RowCt
     auto word = [&](uint32_t i) -> uint32_t { return c.iw[i]; };
     uint32_t n = c.wc - pos;
     bool is_float = false;
-    if (rt < c.md->bound) {
-        const uint32_t *e = idtab_entry(c.tab, c.md->bound, c.md->slots, rt, false);
+    if (rt < c.bound) {
+        const uint32_t *e = idtab_entry(c.tab, c.bound, c.slots, rt, false);
         uint32_t dr = e ? e[2] : NOROW;
         if (dr != NOROW && c.opcol[c.first + dr] == 22) is_float = true;
     }
@@ -499,7 +547,7 @@ __global__ void __launch_bounds__(1024) k_dis_prepass(DP P)
             d.ok = st == S_OK && (long long)(excl + na) <= P.arena_words;
             d.status = st != S_OK ? st : (d.ok ? S_OK : S_CAPACITY);
             d.header_len = (d.ok && P.header) ? header_len(P.words + o) : 0;
-            d.pad = 0;
+            d.named = 0;
             long long fr = P.first_row[m];
             d.item_base = (fr < n_rows ? fr : n_rows) + m;
             P.dm[m] = d;
@@ -547,6 +595,7 @@ __global__ void k_dis_ids(DP P)
         if (op == 5 && wc >= 2 && P.inline_names) {
             uint32_t target = __ldg(P.words + P.off[row] + 1);
             if (target < md.bound) {
+                if (!md.named) P.dm[m].named = 1;
                 atomicMin(&idtab_entry(tab, md.bound, md.slots, target, true)[0], local);
                 if (!md.slots) atomicAnd(&tab[3ull * md.bound + (target >> 5)], ~(1u << (target & 31)));
             }
@@ -595,8 +644,8 @@ constexpr int NSHAPE = 64;
 
 struct MainSmem {
     char text[TEXT_SMEM + 16];
-    long long ibase[ITEMS + 2];     // item_base of modules m0 .. m0 + nm, then the next module's (or n_items)
-    long long irow[ITEMS];          // per item of the tile: its row, -1 for a header item
+    int ibase[ITEMS + 2];           // item_base - i0 of modules m0 .. m0 + nm, then of the next module (or
+                                    // n_items), clamped to [-1, ITEMS + 1]
     int im[ITEMS];                  // per item: its module, -1 past the end
     uint32_t ilen[ITEMS];           // per item: text bytes
     uint32_t ioff[ITEMS];           // per item: offset in the tile's text
@@ -606,6 +655,7 @@ struct MainSmem {
     uint16_t iop[ITEMS], iwc[ITEMS];// per item: opcode and word count
     uint8_t icls[ITEMS];            // per item: shape class
     uint8_t iok[ITEMS];             // per item: operands parse (else raw words)
+    uint8_t ihdr[ITEMS];            // per item: a module's header item
     uint32_t wst[STAGE_WORDS];      // words [wlo, wlo + STAGE_WORDS) of the batch
     unsigned long long wlo, whi;
     uint32_t cls_n[NSHAPE];
@@ -624,7 +674,9 @@ __device__ __forceinline__ bool make_ctx(const DP &P, const MainSmem &s, int j, 
     c.iw = s.irel[j] != NOSTAGE ? s.wst + s.irel[j] : P.words + P.off[row];
     c.wc = s.iwc[j];
     c.op = s.iop[j];
-    c.md = &md;
+    c.bound = md.bound;
+    c.slots = md.slots;
+    c.named = P.inline_names && md.named;
     c.tab = P.arena + md.arena_off;
     c.words = P.words;
     c.off = P.off;
@@ -698,28 +750,35 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
     unsigned int ticket = 0;
     if (tid == 0) ticket = atomicAdd(&P.ctrl->next_tile, 1u);
     for (;;) {
-        if (tid == 0) {
-            s.tile = (long long)ticket;
-            s.gave_up = 0;
-            if ((long long)ticket < ntiles) {
-                long long tt = (long long)ticket;
-                ticket = atomicAdd(&P.ctrl->next_tile, 1u);
-                int m0 = P.tile_m0[tt];
-                int m1 = tt + 1 < ntiles ? P.tile_m0[tt + 1] : P.n_mod - 1;
-                s.m0 = m0;
-                s.nm = m1 - m0 + 1;                  // <= ITEMS + 1
+        // warp 0: the tile, its modules and their first items
+        if (wid == 0) {
+            const long long tt = (long long)__shfl_sync(0xffffffffu, ticket, 0);
+            if (lane == 0) {
+                s.tile = tt;
+                s.gave_up = 0;
+                s.wlo = ~0ull;
+                s.whi = 0;
+                if (tt < ntiles) ticket = atomicAdd(&P.ctrl->next_tile, 1u);
+            }
+            if (tt < ntiles) {
+                const int m0 = P.tile_m0[tt];
+                const int nm = (tt + 1 < ntiles ? P.tile_m0[tt + 1] : P.n_mod - 1) - m0 + 1;   // <= ITEMS + 1
+                if (lane == 0) { s.m0 = m0; s.nm = nm; }
+                const long long i0 = tt * ITEMS;
+                for (int j = lane; j <= nm; j += 32) {
+                    long long b = j < nm ? P.dm[m0 + j].item_base
+                                         : (m0 + nm < P.n_mod ? P.dm[m0 + nm].item_base : n_items);
+                    b -= i0;
+                    s.ibase[j] = (int)(b < -1 ? -1 : (b > ITEMS + 1 ? ITEMS + 1 : b));
+                }
             }
         }
         if (tid < NSHAPE) s.cls_n[tid] = 0;
-        if (tid == 0) { s.wlo = ~0ull; s.whi = 0; }
         __syncthreads();
         const long long t = s.tile;
         if (t >= ntiles) break;
         const long long i0 = t * ITEMS;
         const int m0 = s.m0, nm = s.nm;
-        for (int j = tid; j <= nm; j += DNT)
-            s.ibase[j] = j < nm ? P.dm[m0 + j].item_base : (m0 + nm < P.n_mod ? P.dm[m0 + nm].item_base : n_items);
-        __syncthreads();
 
         // 1. locate every item (op, word count and word offset read once,
         //    coalesced), count the shape classes, find the tile's word range
@@ -728,24 +787,27 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
             for (int j = tid; j < ITEMS; j += DNT) {
                 long long i = i0 + j;
                 int m = -1, cls = 0;
-                long long row = -1;
-                uint32_t op = 0, wc = 0;
+                uint32_t op = 0, wc = 0, olo = 0;
+                bool hdr = false;
                 if (i < n_items) {
-                    int lo = 0, hi = nm;                 // last k with ibase[k] <= i
-                    while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (s.ibase[mid] <= i) lo = mid; else hi = mid; }
+                    int lo = 0, hi = nm;                 // last k with ibase[k] <= j
+                    while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (s.ibase[mid] <= j) lo = mid; else hi = mid; }
                     m = m0 + lo;
-                    if (i != s.ibase[lo]) {
-                        row = P.first_row[m] + (i - s.ibase[lo] - 1);
+                    hdr = j == s.ibase[lo];
+                    if (!hdr) {
+                        long long row = i - m - 1;       // module m's rows follow its header item
                         op = P.op[row];
                         wc = P.wc[row];
                         unsigned long long o = P.off[row];
+                        olo = (uint32_t)o;
                         lo_w = o < lo_w ? o : lo_w;
                         hi_w = o + wc > hi_w ? o + wc : hi_w;
                         cls = op < 256 ? g_spv_tables.shape[op] : 1;
                     }
                 }
                 s.im[j] = m;
-                s.irow[j] = row;
+                s.ihdr[j] = hdr;
+                s.irel[j] = olo;                         // low word offset bits, made relative below
                 s.iop[j] = (uint16_t)op;
                 s.iwc[j] = (uint16_t)wc;
                 s.icls[j] = (uint8_t)cls;
@@ -761,21 +823,18 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
         }
         __syncthreads();
         // stage the words [wlo, min(whi, wlo + STAGE_WORDS)); an item whose
-        // words all lie inside reads them from shared memory
+        // words all lie inside reads them from shared memory. A tile's words
+        // span less than 2^32, so the low 32 bits give the offset from wlo.
         {
             const unsigned long long wlo = s.wlo, whi = s.whi;
             const uint32_t wn = whi > wlo ? (uint32_t)(whi - wlo < STAGE_WORDS ? whi - wlo : STAGE_WORDS) : 0u;
             for (uint32_t k = tid; k < wn; k += DNT) s.wst[k] = P.words[wlo + k];
             for (int j = tid; j < ITEMS; j += DNT) {
-                uint32_t rel = NOSTAGE;
-                if (s.irow[j] >= 0) {
-                    unsigned long long o = P.off[s.irow[j]];
-                    if (o + s.iwc[j] <= wlo + wn) rel = (uint32_t)(o - wlo);
-                }
-                s.irel[j] = rel;
+                uint32_t rel = s.irel[j] - (uint32_t)wlo;
+                bool row = s.im[j] >= 0 && !s.ihdr[j];
+                s.irel[j] = row && rel + s.iwc[j] <= wn ? rel : NOSTAGE;
             }
         }
-        __syncthreads();
         if (wid == 0) {                               // exclusive scan of the class counts
             uint32_t a = s.cls_n[lane], b = s.cls_n[lane + 32];
             uint32_t ia = a, ib = b;
@@ -799,10 +858,10 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
             uint32_t len = 0;
             uint8_t ok = 1;
             if (m >= 0) {
-                if (s.irow[j] < 0) len = P.dm[m].header_len;
+                if (s.ihdr[j]) len = P.dm[m].header_len;
                 else {
                     RowCtx c;
-                    if (make_ctx(P, s, j, m, s.irow[j], c, -1)) { CountSink k; format_row(k, c); len = k.n; ok = c.walk_ok; }
+                    if (make_ctx(P, s, j, m, i0 + j - m - 1, c, -1)) { CountSink k; format_row(k, c); len = k.n; ok = c.walk_ok; }
                 }
             }
             s.ilen[j] = len;
@@ -833,55 +892,76 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
         if (tid == 0) st_release(&P.tstate[t], (t == 0 ? F_INC : F_AGG) | total);
         const bool last_tile = i0 + ITEMS >= n_items;
         const bool staged = total <= (uint32_t)TEXT_SMEM;
+        auto format_item = [&](auto &k, int j) {
+            if (s.ihdr[j]) format_header(k, P.words + P.mod_off[s.im[j]]);
+            else { RowCtx c; make_ctx(P, s, j, s.im[j], i0 + j - s.im[j] - 1, c, s.iok[j]); format_row(k, c); }
+        };
         if (!staged && wid == 0) dis_lookback(P, s, t, total, lane, last_tile);   // oversized tile: its offset first
         __syncthreads();                              // every item's offset (and an oversized tile's base)
-        // 4. format once, in shape order (into shared memory, or straight to
-        //    global memory for oversized tiles)
-        if (staged ? P.text_cap > 0 : (!s.gave_up && s.base + total <= P.text_cap)) {
-            const unsigned long long gbase = staged ? 0 : s.base;
-            for (int q = tid; q < ITEMS; q += DNT) {
-                int j = s.perm[q];
-                if (s.im[j] < 0 || s.ilen[j] == 0) continue;
-                char *dst = staged ? s.text + s.ioff[j] : P.text + gbase + s.ioff[j];
-                WriteSink k{dst};
-                if (s.irow[j] < 0) format_header(k, P.words + P.mod_off[s.im[j]]);
-                else { RowCtx c; make_ctx(P, s, j, s.im[j], s.irow[j], c, s.iok[j]); format_row(k, c); }
-            }
-        }
+        // 4. format once, in shape order, into shared memory; then the offset
         if (staged) {
-            if (wid == 0) dis_lookback(P, s, t, total, lane, last_tile);
-        }
-        __syncthreads();
-        const unsigned long long base = s.base;
-        for (int j = tid; j < ITEMS; j += DNT)
-            if (s.im[j] >= 0 && s.irow[j] < 0) P.text_off[s.im[j]] = base + s.ioff[j];
-        const bool write = !s.gave_up && base + total <= P.text_cap;
-        // copy out: global words wholly inside the tile's byte range are
-        // stored whole, each assembled from two aligned shared words (the
-        // shift between shared and global alignment is the same for the whole
-        // tile); the partial words at either end byte by byte
-        if (write && staged && total) {
-            const unsigned long long g0 = base, g1 = base + total;
-            const unsigned long long w0 = g0 >> 2, w1 = (g1 + 3) >> 2;
-            const bool aligned = (((uintptr_t)P.text) & 3) == 0;
-            const uint32_t sh = (uint32_t)(g0 & 3);          // global word w starts at shared byte 4(w - w0) - sh
-            const uint32_t *sw = reinterpret_cast<const uint32_t *>(s.text);
-            uint32_t *tw = reinterpret_cast<uint32_t *>(P.text);
-            for (unsigned long long w = w0 + tid; w < w1; w += DNT) {
-                unsigned long long gb = w << 2;
-                if (aligned && gb >= g0 && gb + 4 <= g1) {
-                    uint32_t k = (uint32_t)(w - w0);           // >= 1 when sh != 0 (the first word is partial)
-                    uint32_t v = sh == 0 ? sw[k] : __funnelshift_r(sw[k - 1], sw[k], 8 * (4 - sh));
-                    tw[w] = v;
-                } else {
-                    for (int b = 0; b < 4; b++) {
-                        unsigned long long g = gb + b;
-                        if (g >= g0 && g < g1) P.text[g] = s.text[g - g0];
-                    }
+            if (P.text_cap > 0) {
+                for (int q = tid; q < ITEMS; q += DNT) {
+                    int j = s.perm[q];
+                    if (s.im[j] < 0 || s.ilen[j] == 0) continue;
+                    WriteSink k{s.text + s.ioff[j]};
+                    format_item(k, j);
                 }
             }
+            if (wid == 0) dis_lookback(P, s, t, total, lane, last_tile);
+            __syncthreads();
         }
-        __syncthreads();
+        const unsigned long long base = s.base;
+        for (int j = tid; j < ITEMS; j += DNT)
+            if (s.im[j] >= 0 && s.ihdr[j]) P.text_off[s.im[j]] = base + s.ioff[j];
+        const bool write = !s.gave_up && base + total <= P.text_cap;
+        // 5. copy out, window by window of TEXT_SMEM bytes: a tile with more
+        //    text formats each window in turn (a line crossing a window edge
+        //    is formatted once per window it touches, clipped to it)
+        if (write && total) {
+            const uint32_t nwin = staged ? 1u : (total + TEXT_SMEM - 1) / TEXT_SMEM;
+            for (uint32_t r = 0; r < nwin; r++) {
+                const uint32_t lo = r * (uint32_t)TEXT_SMEM, hi = total - lo < (uint32_t)TEXT_SMEM ? total : lo + TEXT_SMEM;
+                if (!staged) {
+                    for (int q = tid; q < ITEMS; q += DNT) {
+                        int j = s.perm[q];
+                        if (s.im[j] < 0 || s.ilen[j] == 0) continue;
+                        const uint32_t a = s.ioff[j], e = a + s.ilen[j];
+                        if (e <= lo || a >= hi) continue;
+                        if (a >= lo && e <= hi) { WriteSink k{s.text + (a - lo)}; format_item(k, j); }
+                        else { ClipSink k{s.text, (long long)a - lo, (long long)(hi - lo)}; format_item(k, j); }
+                    }
+                    __syncthreads();
+                }
+                // global words wholly inside the window's byte range are
+                // stored whole, each assembled from two aligned shared words
+                // (the shift between shared and global alignment is the same
+                // for the whole window); the partial words at either end byte
+                // by byte
+                const unsigned long long g0 = base + lo, g1 = base + hi;
+                const unsigned long long w0 = g0 >> 2, w1 = (g1 + 3) >> 2;
+                const bool aligned = (((uintptr_t)P.text) & 3) == 0;
+                const uint32_t sh = (uint32_t)(g0 & 3);      // global word w starts at shared byte 4(w - w0) - sh
+                const uint32_t *sw = reinterpret_cast<const uint32_t *>(s.text);
+                uint32_t *tw = reinterpret_cast<uint32_t *>(P.text);
+                for (unsigned long long w = w0 + tid; w < w1; w += DNT) {
+                    unsigned long long gb = w << 2;
+                    if (aligned && gb >= g0 && gb + 4 <= g1) {
+                        uint32_t k = (uint32_t)(w - w0);       // >= 1 when sh != 0 (the first word is partial)
+                        uint32_t v = sh == 0 ? sw[k] : __funnelshift_r(sw[k - 1], sw[k], 8 * (4 - sh));
+                        tw[w] = v;
+                    } else {
+                        for (int b = 0; b < 4; b++) {
+                            unsigned long long g = gb + b;
+                            if (g >= g0 && g < g1) P.text[g] = s.text[g - g0];
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        } else {
+            __syncthreads();
+        }
     }
 }
 

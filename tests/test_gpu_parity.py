@@ -398,6 +398,49 @@ def test_long_instructions_cross_tiles(gpu, tile, threads):
     check(gpu, words, offs, cfg=gpu.make_config(tile_words=tile, threads=threads), dis=(tile == 4096))
 
 
+def _window_module(seed):
+    """A module whose text lines are far longer than the disassembler's
+    shared text window: ids with names of thousands of characters (printed
+    at every use), a string of tens of thousands of bytes that need escapes,
+    and many integer and float constants, so that lines cross window edges
+    inside names, escapes, decimals and hex floats."""
+    rng = np.random.default_rng(seed)
+    base = H.minimal_body()
+    head, tail = base[:7], base[7:]
+    alphabet = np.frombuffer(b"abcXYZ019_-. +*/", np.uint8)
+    def name(n):
+        return bytes(alphabet[rng.integers(0, len(alphabet), n)]).decode()
+    body = list(head)
+    body.append(H.ins(H.OpTypeFloat, 50, 32))
+    body.append(H.ins(H.OpTypeFloat, 51, 64))
+    body.append(H.ins(H.OpName, 2, H.s(name(int(rng.integers(3000, 7000))))))
+    body.append(H.ins(H.OpName, 50, H.s(name(int(rng.integers(15000, 25000))))))
+    raw = bytes(int(x) for x in rng.choice([0x22, 0x5c, 0x01, 0x7f, 0x41, 0x61, 0xe9], size=int(rng.integers(30000, 45000))))
+    sw = raw + b"\0" * (4 - len(raw) % 4)
+    body.append(H.ins(H.OpString, 60, [int.from_bytes(sw[i:i + 4], "little") for i in range(0, len(sw), 4)]))
+    nid = 100
+    for k in range(int(rng.integers(300, 500))):
+        kind = int(rng.integers(0, 4))
+        if kind == 0:
+            body.append(H.ins(H.OpConstant, 2, nid, int(rng.integers(0, 2 ** 32))))
+        elif kind == 1:
+            body.append(H.ins(H.OpConstant, 50, nid, int(rng.integers(0, 2 ** 32))))
+        elif kind == 2:
+            body.append(H.ins(H.OpConstant, 51, nid, int(rng.integers(0, 2 ** 32)), int(rng.integers(0, 2 ** 32))))
+        else:
+            body.append(H.ins(H.OpDecorate, nid - 1, 44, int(rng.integers(1, 1 << 20))))    # Alignment
+        nid += 1
+    body.extend(tail)
+    return H.module(body, bound=nid + 1)
+
+
+def test_text_windows_and_lines_longer_than_a_window(gpu):
+    mods = [_window_module(s) for s in range(3)] + [H.module(H.minimal_body(), bound=8)]
+    words, offs = H.batch(mods)
+    g = run(gpu, words, offs)
+    check_dis(gpu, words, offs, g)
+
+
 def test_big_tiles_on_generated_batch(gpu):
     n_instr, n_k = synth.batch_shape(80, 23, median=3000, lo=200, hi=40000)
     w, off = synth.batch(n_instr, n_k, 23)

@@ -377,6 +377,10 @@ def _const_text(bits_words, width=32):
     (0x3DCCCCCD, "0x1.99999ap-4"),   # 0.1f: exponent 123-127=-4, fraction 0x4ccccd<<1
     (0x40490FDB, "0x1.921fb6p+1"),   # float pi
     (0x00000001, "0x1p-149"),        # smallest subnormal float, normal as a double
+    (0x00000003, "0x1.8p-148"),      # 11b x 2^-149 = 1.1b x 2^-148
+    (0x00000005, "0x1.4p-147"),      # 101b x 2^-149 = 1.01b x 2^-147
+    (0x00400000, "0x1p-127"),        # 2^22 x 2^-149
+    (0x007FFFFF, "0x1.fffffcp-127"), # largest subnormal: 1.(22 ones)b x 2^-127
     (0x00000000, "0x0p+0"),
     (0x80000000, "-0x0p+0"),
     (0xC1200000, "-0x1.4p+3"),       # -10
