@@ -132,11 +132,25 @@ class Clocks:
 def algorithmic_bytes(kernel, W, N, L, M):
     return {
         "k_tile": 4 * W + 4 * W + 24 * N,                # words in; encoded words + 24-byte rows out
-        "k_dis_main": 4 * W + 16 * N + L,                # words + op/wc/off/mod in; text out
+        "k_dis_main": 4 * W + 12 * N + L,                # words + op/wc/off columns in; text out
         "k_dis_ids": 20 * N,                             # op/wc/off/mod/rid columns
         "k_dis_namelen": 4 * N,                          # op column (OpName rows are few)
         "k_dis_clear": 0, "k_tile_setup": 0, "k_prepass": 40 * M, "k_finalize": 64 * M,
     }.get(kernel, 0)
+
+
+def issue_roofline(warp_inst, ms, clk):
+    """Instruction-issue view of the dominant kernel: its warp instructions
+    per launch (an ncu count for the same source and workload) over the live
+    launch time, against 148 SMs x 4 schedulers x one warp instruction per
+    cycle at the sampled SM clock."""
+    mhz = clk.get("sm_mhz") if clk else None
+    if not warp_inst or not mhz:
+        return None
+    peak = 148 * 4 * mhz * 1e6
+    achieved = warp_inst / (ms * 1e-3)
+    return {"unit": "warp instructions/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+            "warp_instructions_per_launch": warp_inst, "sm_mhz": mhz}
 
 
 def serve_leg(spvgpu, w_np, off_np, rate, seconds, max_batch_modules=0, pool_size=2000, cap=4 << 30):
@@ -314,11 +328,14 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = alg / (per_launch_ms * 1e-3) / 1e9
     traffic = None
+    warp_inst = None
     tj = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tj):
         t = json.load(open(tj))
-        if t.get("kernel") == kname and t.get("source_sha") == source_hash() and t.get("workload") == args.workload:
+        if (t.get("kernel") == kname and t.get("source_sha") == source_hash() and t.get("workload") == args.workload
+                and t.get("modules") == M):
             traffic = t.get("bytes_per_launch")
+            warp_inst = t.get("warp_instructions_per_launch")
     kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in
                sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
@@ -405,7 +422,8 @@ def main():
         "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": cfg,
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "algorithmic_bytes_per_launch": alg, "ms_per_launch": per_launch_ms},
+                     "algorithmic_bytes_per_launch": alg, "ms_per_launch": per_launch_ms,
+                     "issue": issue_roofline(warp_inst, per_launch_ms, clk)},
         "kernels": kernels,
         "cpu_baseline": cpu,
         "e2e": e2e,
