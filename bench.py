@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--modules", type=int, default=10_000, help="modules in the batch workload")
     ap.add_argument("--serve-rate", type=float, default=20_000.0, help="Poisson arrival rate of the serve leg (modules/s)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="duration of the serve leg (0: skip)")
+    ap.add_argument("--e2e-chunk-words", type=int, default=0, help="chunk size of the end-to-end pipeline (0: library default)")
     return ap.parse_args()
 
 
@@ -84,10 +85,19 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def source_hash():
+# the device-code sources each measured kernel is built from
+KERNEL_SOURCES = {
+    "k_dis_main": ("spv_dis.cu", "spv_device.cuh", "spv_tables.cuh"),
+    "k_tile": ("spv_batch.cu", "spv_device.cuh", "spv_tables.cuh"),
+}
+
+
+def source_hash(kernel):
+    """Hash of the kernel's device-code sources: a stored ncu figure is used
+    only while these are unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_09493_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES.get(kernel, sorted(os.listdir(csrc))):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -332,24 +342,46 @@ def main():
     tj = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tj):
         t = json.load(open(tj))
-        if (t.get("kernel") == kname and t.get("source_sha") == source_hash() and t.get("workload") == args.workload
+        if (t.get("kernel") == kname and t.get("source_sha") == source_hash(kname) and t.get("workload") == args.workload
                 and t.get("modules") == M):
             traffic = t.get("bytes_per_launch")
             warp_inst = t.get("warp_instructions_per_launch")
     kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in
                sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
-    # end to end: pinned host buffers, copies inside the timed region
+    # end to end through spv_pipe_run: the batch in pinned host memory, the
+    # results back in pinned host memory; uploads, kernels and downloads of
+    # successive chunks overlap. The serial chain (one upload, the step, one
+    # download, on one stream) is timed beside it for comparison.
     h_words = torch.from_numpy(w_np.view(np.int32)).pin_memory()
     h_off = torch.from_numpy(off_np).pin_memory()
     h_status = torch.empty(M, dtype=torch.int32).pin_memory()
     h_err = torch.empty(M, dtype=torch.int64).pin_memory()
     h_toff = torch.empty(M + 1, dtype=torch.int64).pin_memory()
     h_text = torch.empty(Ltext + 1, dtype=torch.uint8).pin_memory()
+    pipe = spvgpu.Pipe(chunk_words=args.e2e_chunk_words)
+    pipe.run(h_words, h_off, h_status, h_err, h_toff, h_text)
+    e2e_ok = int(h_toff[M]) == Ltext and bool((h_status == 0).all())
+    ksteps = max(1, min(args.steps, 5))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ksteps):
+        pipe.run(h_words, h_off, h_status, h_err, h_toff, h_text)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / ksteps
+    pipe.close()
+    chunk_words = args.e2e_chunk_words or (8 << 20)
+    n_chunks, a = 0, 0
+    while a < M:                                   # the library's chunking: whole modules, ~chunk_words words
+        b = a + 1
+        while b < M and off_np[b + 1] - off_np[a] <= chunk_words:
+            b += 1
+        n_chunks, a = n_chunks + 1, b
     e_words = torch.empty_like(words)
     e_off = torch.empty_like(mod_off)
 
-    def e2e_step():
+    def serial_step():
         e_words.copy_(h_words, non_blocking=True)
         e_off.copy_(h_off, non_blocking=True)
         rr = spvgpu.process(e_words, e_off, encode=True, table=table, workspace=ws, out=out)
@@ -359,24 +391,24 @@ def main():
         h_toff.copy_(toff, non_blocking=True)
         h_text.copy_(text_buf, non_blocking=True)
 
-    e2e_step()
+    serial_step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ksteps = max(1, min(args.steps, 5))
     e0.record(stream)
     for _ in range(ksteps):
-        e2e_step()
+        serial_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / ksteps
+    serial_ms = e0.elapsed_time(e1) / ksteps
     if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
+        tt = torch.tensor([e2e_ms, serial_ms], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+        e2e_ms, serial_ms = float(tt[0].item()), float(tt[1].item())
     e2e = {"value": world * 4 * W / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": 4 * W + 8 * (M + 1),
-           "d2h_bytes_per_step": 4 * M + 8 * M + 8 * (M + 1) + (Ltext + 1),
-           "ms_per_step": e2e_ms}
+           "h2d_bytes_per_step": 4 * W + 8 * (M + n_chunks),
+           "d2h_bytes_per_step": 4 * M + 8 * M + 8 * (M + n_chunks) + Ltext,
+           "ms_per_step": e2e_ms, "api": "spv_pipe_run", "chunks": n_chunks, "results_exact": e2e_ok,
+           "serial_one_stream": {"ms_per_step": serial_ms, "value": world * 4 * W / (serial_ms * 1e-3) / 1e9}}
 
     # batched vs per-module launches (decode+validate+encode, same exact output)
     cmp = None

@@ -304,6 +304,48 @@ int spv_serve_release(spv_server *s, uint64_t ticket);
 /* Stop the scheduler, wait for in-flight batches, free everything. */
 void spv_serve_destroy(spv_server *s);
 
+/*
+ * Host-resident batches, transfers overlapped with the kernels (a library
+ * service; the paper has no counterpart). A batch that starts and ends in
+ * host memory is bound by the PCIe copies: its words go up once and its text,
+ * several times larger, comes back. spv_pipe_run splits the batch into
+ * chunks of whole modules (about chunk_words words each; a larger module is
+ * a chunk of its own) that rotate over `depth` slots, each with its own
+ * stream and device buffers, so one chunk's text copy-back overlaps the next
+ * chunk's kernels and the upload of the one after.
+ */
+typedef struct spv_pipe spv_pipe;
+typedef struct spv_pipe_cfg {
+    int64_t chunk_words;        /* target words per chunk (0: 8M words) */
+    int32_t depth;              /* slots in flight, 2..8 (0: 3) */
+    int32_t validate;           /* nonzero: validate (else decode-only statuses) */
+    int32_t encode;             /* nonzero: re-encode on the device (copied back when h_out_words != NULL) */
+    int32_t inline_names;       /* disassembly options as in spv_dis_opts */
+    int32_t header;
+} spv_pipe_cfg;
+/* A handle on the current device, holding its slots' streams; device and
+ * pinned buffers are allocated by the first run and grown when a later batch
+ * needs more. NULL on failure. */
+spv_pipe *spv_pipe_create(const spv_pipe_cfg *cfg);
+/*
+ * Process a batch in host memory: h_words[n_words], h_mod_off[n_modules + 1]
+ * (non-decreasing, h_mod_off[n_modules] <= n_words). Outputs, all host
+ * memory: h_status / h_err_row [n_modules] as spv_process_batch;
+ * h_text_off[n_modules + 1] and h_text[text_capacity] as
+ * spv_disassemble_batch over the whole batch (h_text_off[n_modules] is the
+ * total size; no byte at or past text_capacity is written); optional
+ * h_out_words[n_words] (encoded words, needs cfg.encode) and
+ * h_dis_status[n_modules]. Page-locked host buffers let the copies overlap;
+ * pageable ones work but serialise. Returns when every output is in place:
+ * SPV_SUCCESS, SPV_E_ARG (nothing done), SPV_E_CUDA. With n_modules == 0
+ * only h_text_off[0] = 0 is written (the other outputs may be NULL).
+ */
+int spv_pipe_run(spv_pipe *p, const uint32_t *h_words, int64_t n_words, const int64_t *h_mod_off, int32_t n_modules,
+                 uint32_t *h_status, int64_t *h_err_row, uint64_t *h_text_off, char *h_text, uint64_t text_capacity,
+                 uint32_t *h_out_words, uint32_t *h_dis_status);
+/* Wait for the handle's streams, free its buffers and streams. */
+void spv_pipe_destroy(spv_pipe *p);
+
 /* Host-side queries of the library's own opcode / enumerant tables (no GPU
  * needed). spv_op_info returns 0 and fills the outputs for a known opcode,
  * -1 otherwise; cap is the capability the opcode requires or -1. */

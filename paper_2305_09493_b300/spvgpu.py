@@ -459,3 +459,81 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# host-resident batches with overlapped transfers
+# ---------------------------------------------------------------------------
+class SpvPipeCfg(ctypes.Structure):
+    _fields_ = [("chunk_words", ctypes.c_int64), ("depth", ctypes.c_int32), ("validate", ctypes.c_int32),
+                ("encode", ctypes.c_int32), ("inline_names", ctypes.c_int32), ("header", ctypes.c_int32)]
+
+
+def _pipe_lib():
+    lib = load()
+    if not getattr(lib, "_pipe_ready", False):
+        lib.spv_pipe_create.restype = ctypes.c_void_p
+        lib.spv_pipe_create.argtypes = [ctypes.POINTER(SpvPipeCfg)]
+        lib.spv_pipe_run.restype = ctypes.c_int
+        lib.spv_pipe_run.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int32, P, P, P, P, ctypes.c_uint64, P, P]
+        lib.spv_pipe_destroy.restype = None
+        lib.spv_pipe_destroy.argtypes = [P]
+        lib._pipe_ready = True
+    return lib
+
+
+def spv_pipe_create(cfg):
+    return _pipe_lib().spv_pipe_create(ctypes.byref(cfg))
+
+
+def spv_pipe_run(pipe, h_words, n_words, h_mod_off, n_modules, h_status, h_err_row, h_text_off, h_text,
+                 text_capacity, h_out_words, h_dis_status):
+    return _pipe_lib().spv_pipe_run(pipe, h_words, n_words, h_mod_off, n_modules, h_status, h_err_row, h_text_off,
+                                    h_text, text_capacity, h_out_words, h_dis_status)
+
+
+def spv_pipe_destroy(pipe):
+    _pipe_lib().spv_pipe_destroy(pipe)
+
+
+def _host_ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        assert a.device.type == "cpu" and a.is_contiguous()
+        return ctypes.c_void_p(a.data_ptr())
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Pipe:
+    """A batch in host memory through spv_pipe_run (thin wrapper). Arrays are
+    numpy arrays or CPU torch tensors (pinned ones let the copies overlap)."""
+
+    def __init__(self, chunk_words=0, depth=0, validate=True, encode=True, inline_names=True, header=True):
+        self.h = spv_pipe_create(SpvPipeCfg(chunk_words, depth, 1 if validate else 0, 1 if encode else 0,
+                                            1 if inline_names else 0, 1 if header else 0))
+        if not self.h:
+            raise SpvError("spv_pipe_create failed")
+
+    def run(self, words, mod_off, status, err_row, text_off, text, out_words=None, dis_status=None):
+        """Fills the output arrays in place; returns the total text size
+        (text_off[-1]); text holds min(size, len(text)) bytes."""
+        n_mod = len(mod_off) - 1
+        cap = text.numel() if isinstance(text, torch.Tensor) else len(text)
+        rc = spv_pipe_run(self.h, _host_ptr(words), len(words), _host_ptr(mod_off), n_mod, _host_ptr(status),
+                          _host_ptr(err_row), _host_ptr(text_off), _host_ptr(text), cap, _host_ptr(out_words),
+                          _host_ptr(dis_status))
+        _check(rc, "spv_pipe_run")
+        return int(text_off[n_mod])
+
+    def close(self):
+        if self.h:
+            spv_pipe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
