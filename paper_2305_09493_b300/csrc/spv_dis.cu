@@ -19,6 +19,7 @@
 // row of the first instruction defining it (whether an OpConstant's type is
 // a float).
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "../../include/spv.h"
@@ -154,21 +155,33 @@ struct CountSink {
     __device__ __forceinline__ void put(char) { n++; }
     __device__ __forceinline__ void puts(const char *, int len) { n += len; }
 };
+// k_dis_main's dynamic shared memory; its text buffer starts at byte 0. The
+// writing sinks hold byte offsets into it rather than pointers, so every
+// text store is a shared-memory store, also inside the out-of-line helpers
+// that take and return a sink (a pointer passed through them would lose its
+// address space and turn every later store generic).
+extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ char *stext() { return reinterpret_cast<char *>(smem_raw); }
+
 struct WriteSink {
     static constexpr bool counting = false, clipping = false;
-    char *p;
-    __device__ __forceinline__ void put(char c) { *p++ = c; }
-    __device__ __forceinline__ void puts(const char *s, int len) { for (int i = 0; i < len; i++) p[i] = s[i]; p += len; }
+    uint32_t p;                  // byte offset in the shared text buffer
+    __device__ __forceinline__ void put(char c) { stext()[p++] = c; }
+    __device__ __forceinline__ void puts(const char *s, int len)
+    {
+        for (int i = 0; i < len; i++) stext()[p + i] = s[i];
+        p += len;
+    }
 };
-// writes only the bytes of a window [0, lim) of positions; p starts at the
-// line's position relative to the window (possibly negative)
+// writes only the bytes of a window [0, lim) of positions of the shared text
+// buffer; p starts at the line's position relative to the window (possibly
+// negative)
 struct ClipSink {
     static constexpr bool counting = false, clipping = true;
-    char *buf;
     long long p, lim;
     __device__ __forceinline__ void put(char c)
     {
-        if ((unsigned long long)p < (unsigned long long)lim) buf[p] = c;
+        if ((unsigned long long)p < (unsigned long long)lim) stext()[p] = c;
         p++;
     }
     __device__ __forceinline__ void puts(const char *s, int len) { for (int i = 0; i < len; i++) put(s[i]); }
@@ -188,8 +201,8 @@ template <class Sink> __device__ __forceinline__ void put_dec(Sink &k, uint32_t 
         for (int i = (int)dec_len32(v) - 1; i >= 0; i--) k.put((char)('0' + (v / c_pow10[i]) % 10u));
     } else {
         uint32_t n = dec_len32(v);
-        char *e = k.p + n;
-        do { *--e = (char)('0' + v % 10u); v /= 10u; } while (v);
+        uint32_t e = k.p + n;
+        do { stext()[--e] = (char)('0' + v % 10u); v /= 10u; } while (v);
         k.p += n;
     }
 }
@@ -204,12 +217,12 @@ template <class Sink> __device__ __forceinline__ void put_dec(Sink &k, unsigned 
     } else {
         // digits written backwards into place: no local buffer
         uint32_t n = dec_len64(v);
-        char *e = k.p + n;
+        uint32_t e = k.p + n;
         if (!(v >> 32)) {
             uint32_t x = (uint32_t)v;
-            do { *--e = (char)('0' + x % 10u); x /= 10u; } while (x);
+            do { stext()[--e] = (char)('0' + x % 10u); x /= 10u; } while (x);
         } else {
-            do { *--e = (char)('0' + v % 10); v /= 10; } while (v);
+            do { stext()[--e] = (char)('0' + v % 10); v /= 10; } while (v);
         }
         k.p += n;
     }
@@ -740,8 +753,8 @@ __device__ void dis_lookback(const DP &P, MainSmem &s, long long t, uint32_t tot
 // publish, so the look-back seldom waits.
 __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     MainSmem &s = *reinterpret_cast<MainSmem *>(smem_raw);
+    static_assert(offsetof(MainSmem, text) == 0, "the sinks write at offsets from the start of shared memory");
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n_items = (long long)P.ctrl->n_items;
     const long long ntiles = (n_items + ITEMS - 1) / ITEMS;
@@ -904,7 +917,7 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
                 for (int q = tid; q < ITEMS; q += DNT) {
                     int j = s.perm[q];
                     if (s.im[j] < 0 || s.ilen[j] == 0) continue;
-                    WriteSink k{s.text + s.ioff[j]};
+                    WriteSink k{s.ioff[j]};
                     format_item(k, j);
                 }
             }
@@ -928,8 +941,8 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
                         if (s.im[j] < 0 || s.ilen[j] == 0) continue;
                         const uint32_t a = s.ioff[j], e = a + s.ilen[j];
                         if (e <= lo || a >= hi) continue;
-                        if (a >= lo && e <= hi) { WriteSink k{s.text + (a - lo)}; format_item(k, j); }
-                        else { ClipSink k{s.text, (long long)a - lo, (long long)(hi - lo)}; format_item(k, j); }
+                        if (a >= lo && e <= hi) { WriteSink k{a - lo}; format_item(k, j); }
+                        else { ClipSink k{(long long)a - lo, (long long)(hi - lo)}; format_item(k, j); }
                     }
                     __syncthreads();
                 }
