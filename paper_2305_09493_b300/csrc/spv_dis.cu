@@ -669,7 +669,7 @@ struct MainSmem {
     uint8_t icls[ITEMS];            // per item: shape class
     uint8_t iok[ITEMS];             // per item: operands parse (else raw words)
     uint8_t ihdr[ITEMS];            // per item: a module's header item
-    uint32_t wst[STAGE_WORDS];      // words [wlo, wlo + STAGE_WORDS) of the batch
+    alignas(16) uint32_t wst[STAGE_WORDS];  // words [wa, wa + STAGE_WORDS) of the batch (wa: wlo aligned down)
     unsigned long long wlo, whi;
     uint32_t cls_n[NSHAPE];
     uint32_t warp_tot[DNT / 32];
@@ -678,6 +678,21 @@ struct MainSmem {
     int m0, nm;
     int gave_up;
 };
+
+// asynchronous global -> shared copies (completed by cp_async_wait_all and
+// made visible to the block by the next barrier); the 16-byte form reads
+// src_bytes (4..16) and fills the rest of the 16 bytes with zeros
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ bool make_ctx(const DP &P, const MainSmem &s, int j, int m, long long row, RowCtx &c,
                                          int walk_ok)
@@ -794,59 +809,92 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
         const int m0 = s.m0, nm = s.nm;
 
         // 1. locate every item (op, word count and word offset read once,
-        //    coalesced), count the shape classes, find the tile's word range
+        //    coalesced: all of a thread's loads are issued before any is
+        //    used), count the shape classes, find the tile's word range
         {
             unsigned long long lo_w = ~0ull, hi_w = 0;
-            for (int j = tid; j < ITEMS; j += DNT) {
-                long long i = i0 + j;
-                int m = -1, cls = 0;
-                uint32_t op = 0, wc = 0, olo = 0;
+            int mq[IPT];
+            bool hq[IPT];
+            long long rq[IPT];
+            #pragma unroll
+            for (int q = 0; q < IPT; q++) {
+                const int j = tid + q * DNT;
+                const long long i = i0 + j;
+                int m = -1;
                 bool hdr = false;
                 if (i < n_items) {
                     int lo = 0, hi = nm;                 // last k with ibase[k] <= j
                     while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (s.ibase[mid] <= j) lo = mid; else hi = mid; }
                     m = m0 + lo;
                     hdr = j == s.ibase[lo];
-                    if (!hdr) {
-                        long long row = i - m - 1;       // module m's rows follow its header item
-                        op = P.op[row];
-                        wc = P.wc[row];
-                        unsigned long long o = P.off[row];
-                        olo = (uint32_t)o;
-                        lo_w = o < lo_w ? o : lo_w;
-                        hi_w = o + wc > hi_w ? o + wc : hi_w;
-                        cls = op < 256 ? g_spv_tables.shape[op] : 1;
-                    }
                 }
-                s.im[j] = m;
-                s.ihdr[j] = hdr;
-                s.irel[j] = olo;                         // low word offset bits, made relative below
-                s.iop[j] = (uint16_t)op;
-                s.iwc[j] = (uint16_t)wc;
+                mq[q] = m;
+                hq[q] = hdr;
+                rq[q] = m >= 0 && !hdr ? i - m - 1 : -1;  // module m's rows follow its header item
+            }
+            uint32_t opq[IPT], wcq[IPT];
+            unsigned long long oq[IPT];
+            #pragma unroll
+            for (int q = 0; q < IPT; q++) {
+                opq[q] = 0; wcq[q] = 0; oq[q] = 0;
+                if (rq[q] >= 0) { opq[q] = P.op[rq[q]]; wcq[q] = P.wc[rq[q]]; oq[q] = P.off[rq[q]]; }
+            }
+            #pragma unroll
+            for (int q = 0; q < IPT; q++) {
+                const int j = tid + q * DNT;
+                int cls = 0;
+                if (rq[q] >= 0) {
+                    lo_w = oq[q] < lo_w ? oq[q] : lo_w;
+                    hi_w = oq[q] + wcq[q] > hi_w ? oq[q] + wcq[q] : hi_w;
+                    cls = opq[q] < 256 ? g_spv_tables.shape[opq[q]] : 1;
+                }
+                s.im[j] = mq[q];
+                s.ihdr[j] = hq[q];
+                s.irel[j] = (uint32_t)oq[q];             // low word offset bits, made relative below
+                s.iop[j] = (uint16_t)opq[q];
+                s.iwc[j] = (uint16_t)wcq[q];
                 s.icls[j] = (uint8_t)cls;
-                s.rank[j] = (uint16_t)atomicAdd(&s.cls_n[cls], 1u);
+                // rank within the class: one shared atomic per distinct class of the warp
+                const unsigned peers = __match_any_sync(0xffffffffu, cls);
+                const int leader = __ffs(peers) - 1;
+                uint32_t first = 0;
+                if (lane == leader) first = atomicAdd(&s.cls_n[cls], (uint32_t)__popc(peers));
+                first = __shfl_sync(0xffffffffu, first, leader);
+                s.rank[j] = (uint16_t)(first + __popc(peers & ((1u << lane) - 1u)));
             }
             #pragma unroll
             for (int d = 16; d > 0; d >>= 1) {
-                unsigned long long a = __shfl_xor_sync(0xffffffffu, lo_w, d), b = __shfl_xor_sync(0xffffffffu, hi_w, d);
-                lo_w = a < lo_w ? a : lo_w;
-                hi_w = b > hi_w ? b : hi_w;
+                unsigned long long x = __shfl_xor_sync(0xffffffffu, lo_w, d), y = __shfl_xor_sync(0xffffffffu, hi_w, d);
+                lo_w = x < lo_w ? x : lo_w;
+                hi_w = y > hi_w ? y : hi_w;
             }
             if (lane == 0 && hi_w) { atomicMin(&s.wlo, lo_w); atomicMax(&s.whi, hi_w); }
         }
         __syncthreads();
-        // stage the words [wlo, min(whi, wlo + STAGE_WORDS)); an item whose
-        // words all lie inside reads them from shared memory. A tile's words
-        // span less than 2^32, so the low 32 bits give the offset from wlo.
+        // stage the words [wa, min(whi, wa + STAGE_WORDS)) with asynchronous
+        // copies (wa = wlo aligned down to 16 bytes when the words buffer is);
+        // an item whose words all lie inside reads them from shared memory. A
+        // tile's words span less than 2^32, so the low 32 bits of an offset
+        // give its distance from wa.
         {
             const unsigned long long wlo = s.wlo, whi = s.whi;
-            const uint32_t wn = whi > wlo ? (uint32_t)(whi - wlo < STAGE_WORDS ? whi - wlo : STAGE_WORDS) : 0u;
-            for (uint32_t k = tid; k < wn; k += DNT) s.wst[k] = P.words[wlo + k];
-            for (int j = tid; j < ITEMS; j += DNT) {
-                uint32_t rel = s.irel[j] - (uint32_t)wlo;
+            const bool al16 = (((uintptr_t)P.words) & 15) == 0;
+            const unsigned long long wa = whi ? (al16 ? (wlo & ~3ull) : wlo) : 0;
+            const uint32_t wn = whi > wa ? (uint32_t)(whi - wa < STAGE_WORDS ? whi - wa : STAGE_WORDS) : 0u;
+            if (al16) {
+                for (uint32_t k = 4 * tid; k < wn; k += 4 * DNT)
+                    cp_async16(&s.wst[k], P.words + wa + k, wn - k >= 4 ? 16u : 4u * (wn - k));
+            } else {
+                for (uint32_t k = tid; k < wn; k += DNT) cp_async4(&s.wst[k], P.words + wa + k);
+            }
+            #pragma unroll
+            for (int q = 0; q < IPT; q++) {
+                const int j = tid + q * DNT;
+                uint32_t rel = s.irel[j] - (uint32_t)wa;
                 bool row = s.im[j] >= 0 && !s.ihdr[j];
                 s.irel[j] = row && rel + s.iwc[j] <= wn ? rel : NOSTAGE;
             }
+            cp_async_wait_all();
         }
         if (wid == 0) {                               // exclusive scan of the class counts
             uint32_t a = s.cls_n[lane], b = s.cls_n[lane + 32];
