@@ -994,27 +994,42 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
                     }
                     __syncthreads();
                 }
-                // global words wholly inside the window's byte range are
-                // stored whole, each assembled from two aligned shared words
-                // (the shift between shared and global alignment is the same
-                // for the whole window); the partial words at either end byte
-                // by byte
+                // the window's bytes go to [g0, g1): global words (or, with a
+                // 16-byte aligned text buffer, 16-byte chunks) wholly inside
+                // are stored whole, each word assembled from two aligned
+                // shared words (the shift between shared and global alignment
+                // is the same for the whole window); the partial ends byte by
+                // byte
                 const unsigned long long g0 = base + lo, g1 = base + hi;
                 const unsigned long long w0 = g0 >> 2, w1 = (g1 + 3) >> 2;
-                const bool aligned = (((uintptr_t)P.text) & 3) == 0;
                 const uint32_t sh = (uint32_t)(g0 & 3);      // global word w starts at shared byte 4(w - w0) - sh
                 const uint32_t *sw = reinterpret_cast<const uint32_t *>(s.text);
-                uint32_t *tw = reinterpret_cast<uint32_t *>(P.text);
-                for (unsigned long long w = w0 + tid; w < w1; w += DNT) {
-                    unsigned long long gb = w << 2;
-                    if (aligned && gb >= g0 && gb + 4 <= g1) {
-                        uint32_t k = (uint32_t)(w - w0);       // >= 1 when sh != 0 (the first word is partial)
-                        uint32_t v = sh == 0 ? sw[k] : __funnelshift_r(sw[k - 1], sw[k], 8 * (4 - sh));
-                        tw[w] = v;
-                    } else {
-                        for (int b = 0; b < 4; b++) {
-                            unsigned long long g = gb + b;
-                            if (g >= g0 && g < g1) P.text[g] = s.text[g - g0];
+                auto gword = [&](uint32_t k) -> uint32_t {   // k = w - w0 (>= 1 when sh != 0)
+                    return sh == 0 ? sw[k] : __funnelshift_r(sw[k - 1], sw[k], 8 * (4 - sh));
+                };
+                if ((((uintptr_t)P.text) & 15) == 0) {
+                    const unsigned long long c0 = (g0 + 15) >> 4, c1 = g1 >> 4;   // whole chunks [c0, c1)
+                    uint4 *t4 = reinterpret_cast<uint4 *>(P.text);
+                    for (unsigned long long c = c0 + tid; c < c1; c += DNT) {
+                        const uint32_t k = (uint32_t)((c << 2) - w0);
+                        t4[c] = make_uint4(gword(k), gword(k + 1), gword(k + 2), gword(k + 3));
+                    }
+                    const unsigned long long h1 = (c0 << 4) < g1 ? (c0 << 4) : g1;
+                    for (unsigned long long g = g0 + tid; g < h1; g += DNT) P.text[g] = s.text[g - g0];
+                    if (c1 >= c0)
+                        for (unsigned long long g = (c1 << 4) + tid; g < g1; g += DNT) P.text[g] = s.text[g - g0];
+                } else {
+                    const bool aligned = (((uintptr_t)P.text) & 3) == 0;
+                    uint32_t *tw = reinterpret_cast<uint32_t *>(P.text);
+                    for (unsigned long long w = w0 + tid; w < w1; w += DNT) {
+                        unsigned long long gb = w << 2;
+                        if (aligned && gb >= g0 && gb + 4 <= g1) {
+                            tw[w] = gword((uint32_t)(w - w0));
+                        } else {
+                            for (int b = 0; b < 4; b++) {
+                                unsigned long long g = gb + b;
+                                if (g >= g0 && g < g1) P.text[g] = s.text[g - g0];
+                            }
                         }
                     }
                 }

@@ -307,6 +307,27 @@ def test_text_capacity_reports_size(gpu):
     assert bool((text == 7).all())
 
 
+def test_text_buffer_at_any_alignment(gpu):
+    """The tile copy-out stores 16-byte chunks when the text buffer is 16-byte
+    aligned, 4-byte words when it is 4-byte aligned, else bytes: text written
+    at every start offset 0..15 equals the oracle's, and the bytes around it
+    stay untouched."""
+    n_instr, n_k = synth.batch_shape(40, 19, median=1500, lo=200, hi=20000)
+    w, off = synth.batch(n_instr, n_k, 19)
+    g = run(gpu, w, off)
+    want, woff = oracle.disassemble(w, off, True, True)
+    big = torch.full((len(want) + 64,), 0xCD, dtype=torch.uint8, device="cuda")
+    for shift in range(16):
+        big.fill_(0xCD)
+        view = big[shift:shift + len(want)]
+        _, toff, _ = gpu.disassemble(g["_w"], g["_o"], g["_r"]["table"], text=view, sync=False)
+        torch.cuda.synchronize()
+        b = big.cpu().numpy()
+        assert bytes(b[shift:shift + len(want)]) == want, shift
+        assert (b[:shift] == 0xCD).all() and (b[shift + len(want):] == 0xCD).all(), shift
+        assert np.array_equal(toff.cpu().numpy(), woff)
+
+
 def test_bounded_wait_times_out_without_hanging(gpu):
     w, off, _, _ = synth.large_module(6, n_instr=60_000, n_funcs=4)
     cfg = gpu.make_config(tile_words=1024, threads=128, max_spins=2000, test_stall_tile=5)
