@@ -44,6 +44,15 @@ constexpr unsigned long long F_MAP = 1ull << 62, F_EXIT = 2ull << 62, F_MASK = 3
 
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }   // one spare word per 16: conflict-free segments
 
+// What a tile of k_tile needs to know about itself, one 32-byte load.
+struct TileRec {
+    long long base;          // the module's first word
+    uint32_t m, k;           // module, tile index within the module
+    uint32_t len_rel;        // module words from this tile's first word (0 for a module too large)
+    uint32_t hdr;            // the module's header status
+    uint32_t pad[2];
+};
+
 struct Params {
     const uint32_t *words;
     const int64_t *mod_off;
@@ -55,13 +64,14 @@ struct Params {
     uint32_t *out;                 // encode target or null
     int validate, recompute_bound;
     // workspace
-    Ctrl *ctrl; int64_t *tile_off; uint32_t *tile_mod; unsigned long long *tstate; uint32_t *tmap;
+    Ctrl *ctrl; int64_t *tile_off; TileRec *tile_rec; unsigned long long *tstate; uint32_t *tmap;
     unsigned long long *cstate; ModState *ms; uint32_t *arena; int64_t arena_words; uint32_t *fixlist;
     int64_t *abase;                // [n_modules + 1] prefix of the id-set words each module asks for
     long long max_spins;
     long long stall_tile;          // test hook: this tile never publishes its look-back states (-1: none)
     int persistent;
     int table_mode;                // validating a caller's table: never write its columns
+    int tile_words;                // words per tile of k_tile
 };
 
 // ---------------------------------------------------------------------------
@@ -141,7 +151,8 @@ __global__ void __launch_bounds__(1024) k_prepass(Params P, int tile_words)
     }
 }
 
-// per tile: owning module, cleared look-back states; clears the id arena
+// per tile: its record (owning module and where it starts), cleared
+// look-back states; clears the id arena
 __global__ void k_tile_setup(Params P)
 {
     unsigned long long nt = P.ctrl->n_tiles;
@@ -152,7 +163,15 @@ __global__ void k_tile_setup(Params P)
             int mid = (lo + hi) >> 1;
             if (P.tile_off[mid] <= g) lo = mid; else hi = mid;
         }
-        P.tile_mod[g] = (uint32_t)lo;
+        TileRec r{};
+        r.m = (uint32_t)lo;
+        r.k = (uint32_t)(g - P.tile_off[lo]);
+        r.base = P.mod_off[lo];
+        r.hdr = P.ms[lo].hdr;
+        long long lr = (P.mod_off[lo + 1] - r.base) - (long long)r.k * P.tile_words;
+        if (r.hdr == S_CAPACITY) lr = 0;
+        r.len_rel = (uint32_t)(lr < 0 ? 0 : lr);
+        P.tile_rec[g] = r;
         P.tstate[g] = 0;
         P.cstate[g] = 0;
     }
@@ -202,43 +221,43 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const spvt::Tables &TB = g_spv_tables;
 
+    // a ticket is taken only when its tile starts: tiles wait on their
+    // predecessors' published states, and a ticket held while its CTA works
+    // on another tile would stall every later tile of the module
+    const long long n_tiles = (long long)P.ctrl->n_tiles;
     for (;;) {
         if (tid == 0) {
-            s.tile = (long long)atomicAdd(&P.ctrl->next_tile, 1u);
+            const long long g0 = (long long)atomicAdd(&P.ctrl->next_tile, 1u);
+            s.tile = g0;
+            if (g0 < n_tiles) {
+                const TileRec r = P.tile_rec[g0];
+                s.m = (int)r.m; s.k = r.k; s.mod_base = r.base; s.hdr = r.hdr;
+                s.len_rel = r.len_rel;
+                s.tile_n = r.len_rel < (uint32_t)T ? r.len_rel : (uint32_t)T;
+                s.timeout = 0;
+                s.err_key = NO_KEY;
+                s.n_cap = s.n_mm = s.n_ep = s.n_fn = 0;
+                s.decl_lo = s.decl_hi = s.req_lo = s.req_hi = 0;
+                s.max_rid = 0; s.flags = 0; s.n_ids = 0;
+            }
         }
         __syncthreads();
         const long long g = s.tile;
-        if (g >= (long long)P.ctrl->n_tiles) break;
-        if (tid == 0) {
-            int m = (int)P.tile_mod[g];
-            long long first = P.tile_off[m];
-            long long base = P.mod_off[m];
-            long long len = P.mod_off[m + 1] - base;
-            uint32_t k = (uint32_t)(g - first);
-            s.m = m; s.k = k; s.mod_base = base;
-            s.hdr = P.ms[m].hdr;
-            long long lr = len - (long long)k * T;
-            if (s.hdr == S_CAPACITY) lr = 0;
-            s.len_rel = (uint32_t)(lr < 0 ? 0 : lr);
-            s.tile_n = s.len_rel < (uint32_t)T ? s.len_rel : (uint32_t)T;
-            s.timeout = 0;
-            s.err_key = NO_KEY;
-            s.n_cap = s.n_mm = s.n_ep = s.n_fn = 0;
-            s.decl_lo = s.decl_hi = s.req_lo = s.req_hi = 0;
-            s.max_rid = 0; s.flags = 0; s.n_ids = 0;
-        }
-        __syncthreads();
+        if (g >= n_tiles) break;
         const uint32_t len_rel = s.len_rel, tile_n = s.tile_n, k = s.k;
         const int m = s.m;
         const bool live = (s.hdr == S_OK);
         const uint32_t *src = P.words + s.mod_base + (long long)k * T;
 
-        // 1. stage
+        // 1. stage, with asynchronous copies (one round trip for the tile)
         {
             int nload = (int)(len_rel < (uint32_t)(T + HALO) ? len_rel : (uint32_t)(T + HALO));
             if (!live) nload = 0;
-            #pragma unroll 4
-            for (int i = tid; i < T + HALO; i += NT) s.w[pad(i)] = i < nload ? __ldg(src + i) : 0u;
+            for (int i = tid; i < T + HALO; i += NT) {
+                if (i < nload) cp_async4(&s.w[pad(i)], src + i);
+                else s.w[pad(i)] = 0u;
+            }
+            cp_async_wait_all();
         }
         __syncthreads();
         auto word = [&](uint32_t p) -> uint32_t { return p < (uint32_t)(T + HALO) ? s.w[pad((int)p)] : __ldg(src + p); };
@@ -880,7 +899,7 @@ __global__ void k_encode_rows(const uint32_t *words, const int64_t *mod_off, con
 // host side
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t ctrl, tile_off, tile_mod, tstate, tmap, cstate, ms, fixlist, abase, arena, total;
+    size_t ctrl, tile_off, tile_rec, tstate, tmap, cstate, ms, fixlist, abase, arena, total;
     long long max_tiles, arena_words;
 };
 
@@ -894,7 +913,7 @@ Layout make_layout(int n_mod, long long n_words, long long arena_words, int tile
     size_t o = 0;
     L.ctrl = o; o = al(o + sizeof(Ctrl));
     L.tile_off = o; o = al(o + 8 * (size_t)(n_mod + 1));
-    L.tile_mod = o; o = al(o + 4 * (size_t)L.max_tiles);
+    L.tile_rec = o; o = al(o + sizeof(TileRec) * (size_t)L.max_tiles);
     L.tstate = o; o = al(o + 8 * (size_t)L.max_tiles);
     L.tmap = o; o = al(o + 4 * (size_t)NCAND * L.max_tiles);
     L.cstate = o; o = al(o + 8 * (size_t)L.max_tiles);
@@ -984,14 +1003,15 @@ bool check_batch(const spv_batch *b)
     return b && b->n_modules >= 0 && b->n_words >= 0 && (b->n_words == 0 || b->words) && b->mod_off;
 }
 
-Params base_params(const spv_batch *b, void *ws, const Layout &L)
+Params base_params(const spv_batch *b, void *ws, const Layout &L, int tile_words)
 {
     Params P{};
+    P.tile_words = tile_words;
     char *w = (char *)ws;
     P.words = b->words; P.mod_off = b->mod_off; P.n_modules = b->n_modules;
     P.ctrl = (Ctrl *)(w + L.ctrl);
     P.tile_off = (int64_t *)(w + L.tile_off);
-    P.tile_mod = (uint32_t *)(w + L.tile_mod);
+    P.tile_rec = (TileRec *)(w + L.tile_rec);
     P.tstate = (unsigned long long *)(w + L.tstate);
     P.tmap = (uint32_t *)(w + L.tmap);
     P.cstate = (unsigned long long *)(w + L.cstate);
@@ -1041,7 +1061,7 @@ extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint3
     if (!workspace || workspace_bytes < L.total) return SPV_E_WORKSPACE;
     if (batch->n_modules == 0) return SPV_SUCCESS;
     cudaStream_t st = (cudaStream_t)stream;
-    Params P = base_params(batch, workspace, L);
+    Params P = base_params(batch, workspace, L, c.T);
     P.op = table->op; P.wc = table->wc; P.off = table->off; P.rtype = table->rtype; P.rid = table->rid;
     P.mod = table->mod; P.first_row = table->mod_first_row; P.n_instr = table->mod_n_instr;
     P.cap_rows = table->capacity_rows;
@@ -1101,7 +1121,7 @@ extern "C" int spv_validate_batch(const spv_batch *batch, const spv_table *table
     if (!workspace || workspace_bytes < L.total) return SPV_E_WORKSPACE;
     if (batch->n_modules == 0) return SPV_SUCCESS;
     cudaStream_t st = (cudaStream_t)stream;
-    Params P = base_params(batch, workspace, L);
+    Params P = base_params(batch, workspace, L, c.T);
     P.op = table->op; P.wc = table->wc; P.off = table->off; P.rtype = table->rtype; P.rid = table->rid;
     P.mod = table->mod; P.first_row = table->mod_first_row; P.n_instr = table->mod_n_instr;
     P.cap_rows = table->capacity_rows;

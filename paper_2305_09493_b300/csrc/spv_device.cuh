@@ -156,6 +156,21 @@ __device__ __forceinline__ uint64_t cap_closure(uint64_t d)
     return d;
 }
 
+// asynchronous global -> shared copies (completed by cp_async_wait_all and
+// made visible to the block by the next barrier); the 16-byte form reads
+// src_bytes (4..16) and fills the rest of the 16 bytes with zeros
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ---------------- literal strings ----------------
 // Words [pos, wc) hold a NUL-terminated string whose last word is zero
 // after the NUL. Returns the word count of the string, or 0 when malformed.

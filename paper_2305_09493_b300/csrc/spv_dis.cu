@@ -187,11 +187,11 @@ struct ClipSink {
     __device__ __forceinline__ void puts(const char *s, int len) { for (int i = 0; i < len; i++) put(s[i]); }
 };
 
-template <class Sink> __device__ __forceinline__ void put_lit(Sink &k, const char *s)
+// a string literal, its length known at compile time
+template <class Sink, int N> __device__ __forceinline__ void put_lit(Sink &k, const char (&s)[N])
 {
-    int n = 0;
-    while (s[n]) n++;
-    k.puts(s, n);
+    #pragma unroll
+    for (int i = 0; i < N - 1; i++) k.put(s[i]);
 }
 template <class Sink> __device__ __forceinline__ void put_dec(Sink &k, uint32_t v)
 {
@@ -256,7 +256,7 @@ template <class Sink> __device__ __noinline__ Sink put_hexfloat64(Sink k, unsign
     bool neg = b >> 63;
     unsigned e = (unsigned)((b >> 52) & 0x7ff);
     unsigned long long m = b & ((1ull << 52) - 1);
-    if (e == 0x7ff) { if (neg) k.put('-'); put_lit(k, m ? "nan" : "inf"); return k; }
+    if (e == 0x7ff) { if (neg) k.put('-'); if (m) put_lit(k, "nan"); else put_lit(k, "inf"); return k; }
     if (neg) k.put('-');
     if (e == 0 && m == 0) { put_lit(k, "0x0p+0"); return k; }
     k.put('0'); k.put('x'); k.put(e == 0 ? '0' : '1');
@@ -678,21 +678,6 @@ struct MainSmem {
     int m0, nm;
     int gave_up;
 };
-
-// asynchronous global -> shared copies (completed by cp_async_wait_all and
-// made visible to the block by the next barrier); the 16-byte form reads
-// src_bytes (4..16) and fills the rest of the 16 bytes with zeros
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes)
-{
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src)
-{
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ bool make_ctx(const DP &P, const MainSmem &s, int j, int m, long long row, RowCtx &c,
                                          int walk_ok)
