@@ -431,19 +431,37 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
         for (int d = 1; d < 32; d <<= 1) { unsigned v = __shfl_up_sync(0xffffffffu, incl, d); if (lane >= d) incl += v; }
         if (lane == 31) s.warp_tot[wid] = incl;
         __syncthreads();
-        if (wid == 0) {
+        const bool stalled = (g == P.stall_tile);
+        if (wid == 0) {                          // block scan of the warp counts; publish the tile's count
             unsigned v = lane < NW ? s.warp_tot[lane] : 0;
             #pragma unroll
             for (int d = 1; d < 32; d <<= 1) { unsigned u = __shfl_up_sync(0xffffffffu, v, d); if (lane >= d) v += u; }
             if (lane < NW) s.warp_tot[lane] = v;
             unsigned total = __shfl_sync(0xffffffffu, v, NW - 1);
-            // 3b. row base from the predecessors' counts (decoupled look-back over all tiles)
+            if (lane == 0) {
+                s.count = total;
+                if (!stalled) st_release(&P.cstate[g], (g == 0 ? F_EXIT : F_MAP) | total);
+            }
+        }
+        __syncthreads();
+        const unsigned tile_count = s.count;
+        const unsigned my_off = (wid ? s.warp_tot[wid - 1] : 0) + incl - cnt;
+        // error keys hold tile-local rows until the flush adds the tile's first row
+        if (ferr >= 0 && live) atomicMin(&s.err_key, make_key(my_off + cnt, R_FRAME, (uint32_t)ferr));
+        // 4. start list (reuses E)
+        uint16_t *S16 = reinterpret_cast<uint16_t *>(s.E);
+        {
+            uint32_t x = mask;
+            unsigned o = my_off;
+            while (x) { int b = __ffs(x) - 1; x &= x - 1; S16[o++] = (uint16_t)(tid * L + b); }
+        }
+        __syncthreads();
+        // 4a. warp 0: the tile's first row (decoupled look-back over all tiles'
+        //     counts); meanwhile the other warps validate the tile's rows,
+        //     which needs no global row index
+        if (wid == 0) {
             unsigned long long excl = 0;
-            const bool stalled = (g == P.stall_tile);
-            if (g == 0) {
-                if (lane == 0 && !stalled) st_release(&P.cstate[0], F_EXIT | total);
-            } else {
-                if (lane == 0 && !stalled) st_release(&P.cstate[g], F_MAP | total);
+            if (g > 0) {
                 long long hi_j = g - 1;
                 long long spins = 0;
                 bool gave_up = false;
@@ -468,98 +486,96 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                     hi_j -= 32;
                 }
                 if (gave_up) { excl = 0; if (lane == 0) s.timeout = 1; }
-                if (lane == 0 && !stalled) st_release(&P.cstate[g], F_EXIT | (excl + total));
+                if (lane == 0 && !stalled) st_release(&P.cstate[g], F_EXIT | (excl + tile_count));
             }
             if (lane == 0) {
                 s.row_base = excl;
-                s.count = total;
                 if (k == 0) P.first_row[m] = (int64_t)excl;
-                if (g == (long long)P.ctrl->n_tiles - 1) P.ctrl->total_rows = excl + total;
+                if (g == n_tiles - 1) P.ctrl->total_rows = excl + tile_count;
             }
-        }
-        __syncthreads();
-        const unsigned long long row_base = s.row_base;
-        const unsigned tile_count = s.count;
-        const unsigned my_off = (wid ? s.warp_tot[wid - 1] : 0) + incl - cnt;
-        if (ferr >= 0 && live) {
-            unsigned long long key = make_key(row_base + my_off + cnt, R_FRAME, (uint32_t)ferr);
-            atomicMin(&s.err_key, key);
-        }
-        // 4. start list (reuses E), then one row per thread
-        uint16_t *S16 = reinterpret_cast<uint16_t *>(s.E);
-        {
-            uint32_t x = mask;
-            unsigned o = my_off;
-            while (x) { int b = __ffs(x) - 1; x &= x - 1; S16[o++] = (uint16_t)(tid * L + b); }
-        }
-        __syncthreads();
-        const uint32_t bound = P.ms[m].bound;
-        const long long arena_off = P.validate ? P.ms[m].arena_off : -1;
-        const uint32_t id_slots = P.ms[m].id_slots;
-        for (unsigned rb = 0; rb < tile_count; rb += NT) {
-            const unsigned r = rb + tid;
-            const bool valid = r < tile_count;
-            uint32_t ri = 0;
-            uint64_t req = 0;
-            uint32_t inserted = 0;
-            if (valid) {
-            uint32_t p = S16[r];
-            uint32_t w0 = word(p);
-            uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
-            const spvt::OpDesc &d = TB.ops[op < 256 ? op : 0];
-            bool known = op < 256 && (d.flags & 1);
-            uint32_t rt = 0;
-            if (known) {
-                uint32_t q = 1;
-                if (d.flags & 2) { if (q < wc) rt = word(p + q); q++; }
-                if (d.flags & 4) { if (q < wc) ri = word(p + q); }
-            }
-            unsigned long long row = row_base + r;
-            if ((long long)row < P.cap_rows) {
-                P.op[row] = (uint16_t)op; P.wc[row] = (uint16_t)wc;
-                P.off[row] = (uint64_t)(s.mod_base + (long long)k * T + p);
-                P.rtype[row] = rt; P.rid[row] = ri; P.mod[row] = (uint32_t)m;
-            } else {
-                atomicOr(&s.flags, MF_CAPACITY);
-            }
-            if (P.validate) {
-                if (op == 17) { atomicAdd(&s.n_cap, 1u); if (wc >= 2) { uint32_t c = word(p + 1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); } }
-                else if (op == 14) atomicAdd(&s.n_mm, 1u);
-                else if (op == 15) atomicAdd(&s.n_ep, 1u);
-                else if (op == 54) atomicAdd(&s.n_fn, 1u);
-                if (!known) { atomicMin(&s.err_key, make_key(row, R_UNKNOWN, 0)); }
-                else {
-                    auto iw = [&](uint32_t i) -> uint32_t { return word(p + i); };
-                    Walk wk = walk_instruction(iw, wc, d, bound);
-                    if (!wk.ok) atomicMin(&s.err_key, make_key(row, R_BADOP, 0));
-                    else if (wk.oob) atomicMin(&s.err_key, make_key(row, R_OOB, 0));
+        } else if (P.validate) {
+            const uint32_t bound = P.ms[m].bound;
+            const long long arena_off = P.ms[m].arena_off;
+            const uint32_t id_slots = P.ms[m].id_slots;
+            for (unsigned rb = 0; rb < tile_count; rb += NT - 32) {
+                const unsigned r = rb + (unsigned)(tid - 32);
+                uint32_t ri = 0;
+                uint64_t req = 0;
+                uint32_t inserted = 0;
+                if (r < tile_count) {
+                    uint32_t p = S16[r];
+                    uint32_t w0 = word(p);
+                    uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
+                    const spvt::OpDesc &d = TB.ops[op < 256 ? op : 0];
+                    bool known = op < 256 && (d.flags & 1);
+                    if (known && (d.flags & 4)) {
+                        uint32_t q = (d.flags & 2) ? 2u : 1u;
+                        if (q < wc) ri = word(p + q);
+                    }
+                    if (op == 17) { atomicAdd(&s.n_cap, 1u); if (wc >= 2) { uint32_t c = word(p + 1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); } }
+                    else if (op == 14) atomicAdd(&s.n_mm, 1u);
+                    else if (op == 15) atomicAdd(&s.n_ep, 1u);
+                    else if (op == 54) atomicAdd(&s.n_fn, 1u);
+                    if (!known) { atomicMin(&s.err_key, make_key(r, R_UNKNOWN, 0)); }
                     else {
-                        if ((d.flags & 4) && arena_off >= 0) {
-                            if (id_slots == 0) {
-                                // no wait on the old value: duplicates show up later as
-                                // fewer bits set than ids inserted
-                                atomicOr(&P.arena[arena_off + (ri >> 5)], 1u << (ri & 31));
-                                inserted = 1;
-                            } else if (idset_insert(P.arena + arena_off, id_slots, ri)) {
-                                atomicOr(&s.flags, MF_DUP);
+                        auto iw = [&](uint32_t i) -> uint32_t { return word(p + i); };
+                        Walk wk = walk_instruction(iw, wc, d, bound);
+                        if (!wk.ok) atomicMin(&s.err_key, make_key(r, R_BADOP, 0));
+                        else if (wk.oob) atomicMin(&s.err_key, make_key(r, R_OOB, 0));
+                        else {
+                            if ((d.flags & 4) && arena_off >= 0) {
+                                if (id_slots == 0) {
+                                    // no wait on the old value: duplicates show up later as
+                                    // fewer bits set than ids inserted
+                                    atomicOr(&P.arena[arena_off + (ri >> 5)], 1u << (ri & 31));
+                                    inserted = 1;
+                                } else if (idset_insert(P.arena + arena_off, id_slots, ri)) {
+                                    atomicOr(&s.flags, MF_DUP);
+                                }
                             }
+                            req = wk.req | width_caps(iw, op, wc);
                         }
-                        req = wk.req | width_caps(iw, op, wc);
                     }
                 }
+                // warp-level aggregation, then one shared atomic per warp
+                uint32_t rlo = __reduce_or_sync(0xffffffffu, (uint32_t)req);
+                uint32_t rhi = __reduce_or_sync(0xffffffffu, (uint32_t)(req >> 32));
+                uint32_t nins = __reduce_add_sync(0xffffffffu, inserted);
+                if (lane == 0) {
+                    if (rlo) atomicOr(&s.req_lo, rlo);
+                    if (rhi) atomicOr(&s.req_hi, rhi);
+                    if (nins) atomicAdd(&s.n_ids, nins);
+                }
             }
+        }
+        __syncthreads();
+        // 4b. the table rows, at the tile's first row; the largest result id
+        const unsigned long long row_base = s.row_base;
+        for (unsigned rb = 0; rb < tile_count; rb += NT) {
+            const unsigned r = rb + tid;
+            uint32_t ri = 0;
+            if (r < tile_count) {
+                uint32_t p = S16[r];
+                uint32_t w0 = word(p);
+                uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
+                const spvt::OpDesc &d = TB.ops[op < 256 ? op : 0];
+                uint32_t rt = 0;
+                if (op < 256 && (d.flags & 1)) {
+                    uint32_t q = 1;
+                    if (d.flags & 2) { if (q < wc) rt = word(p + q); q++; }
+                    if (d.flags & 4) { if (q < wc) ri = word(p + q); }
+                }
+                unsigned long long row = row_base + r;
+                if ((long long)row < P.cap_rows) {
+                    P.op[row] = (uint16_t)op; P.wc[row] = (uint16_t)wc;
+                    P.off[row] = (uint64_t)(s.mod_base + (long long)k * T + p);
+                    P.rtype[row] = rt; P.rid[row] = ri; P.mod[row] = (uint32_t)m;
+                } else {
+                    atomicOr(&s.flags, MF_CAPACITY);
+                }
             }
-            // warp-level aggregation, then one shared atomic per warp
             uint32_t mx = __reduce_max_sync(0xffffffffu, ri);
-            uint32_t rlo = __reduce_or_sync(0xffffffffu, (uint32_t)req);
-            uint32_t rhi = __reduce_or_sync(0xffffffffu, (uint32_t)(req >> 32));
-            uint32_t nins = __reduce_add_sync(0xffffffffu, inserted);
-            if (lane == 0) {
-                if (mx) atomicMax(&s.max_rid, mx);
-                if (rlo) atomicOr(&s.req_lo, rlo);
-                if (rhi) atomicOr(&s.req_hi, rhi);
-                if (nins) atomicAdd(&s.n_ids, nins);
-            }
+            if (lane == 0 && mx) atomicMax(&s.max_rid, mx);
         }
         // 5. encode. In the fused path every field an instruction writes back
         // (first word from wc/op, result type, result id) was just decoded from
@@ -578,7 +594,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
         // 6. flush the tile's aggregates to the module
         if (tid == 0) {
             ModState *ms = &P.ms[m];
-            if (s.err_key != NO_KEY) atomicMin(&ms->err_key, s.err_key);
+            if (s.err_key != NO_KEY) atomicMin(&ms->err_key, s.err_key + (s.row_base << 8));
             if (s.n_cap) atomicAdd(&ms->n_cap, s.n_cap);
             if (s.n_mm) atomicAdd(&ms->n_mm, s.n_mm);
             if (s.n_ep) atomicAdd(&ms->n_ep, s.n_ep);
