@@ -145,7 +145,7 @@ def algorithmic_bytes(kernel, W, N, L, M):
         "k_dis_main": 4 * W + 12 * N + L,                # words + op/wc/off columns in; text out
         "k_dis_ids": 20 * N,                             # op/wc/off/mod/rid columns
         "k_dis_namelen": 4 * N,                          # op column (OpName rows are few)
-        "k_dis_clear": 0, "k_tile_setup": 0, "k_prepass": 40 * M, "k_finalize": 64 * M,
+        "k_dis_clear": 0, "k_tile_setup": 0, "k_prepass_mod": 40 * M, "k_prepass_scan": 24 * M, "k_finalize": 64 * M,
     }.get(kernel, 0)
 
 

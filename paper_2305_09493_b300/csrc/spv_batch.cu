@@ -75,9 +75,39 @@ struct Params {
 };
 
 // ---------------------------------------------------------------------------
-// prepass: headers, tile layout and id-bitmap layout (one CTA of 1024 threads)
+// prepass, in two kernels: per module (many CTAs) the header status, bound,
+// tile count and id-set words; then one CTA scans the counts into the tile
+// and id-set layout
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_prepass(Params P, int tile_words)
+__global__ void k_prepass_mod(Params P, int tile_words)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long mm = blockIdx.x * (long long)blockDim.x + threadIdx.x; mm < P.n_modules; mm += stride) {
+        const int m = (int)mm;
+        unsigned long long nt = 0, nb = 0;
+        uint32_t hdr = S_OK, bound = 0, flags = 0;
+        long long o = P.mod_off[m], len = P.mod_off[m + 1] - o;
+        if (len < 0 || len > 0x7fffffffLL) { hdr = S_CAPACITY; flags = MF_CAPACITY; len = 0; }
+        else hdr = header_status(P.words + o, len);
+        if (len >= 4) bound = P.words[o + 3];
+        nt = len > 0 ? ((unsigned long long)len + (unsigned)tile_words - 1) >> (31 - __clz(tile_words)) : 1;  // tile_words: a power of two
+        if (hdr == S_OK && P.validate) nb = idset_words(bound, len);
+        P.tile_off[m] = (int64_t)nt;              // counts; k_prepass_scan makes them offsets
+        P.abase[m] = (int64_t)nb;
+        ModState st;
+        st.hdr = hdr; st.bound = bound; st.err_key = NO_KEY;
+        st.n_cap = st.n_mm = st.n_ep = st.n_fn = 0;
+        st.decl_lo = st.decl_hi = st.req_lo = st.req_hi = 0;
+        st.max_rid = 0;
+        st.arena_off = -1;
+        st.id_slots = 0; st.n_ids = 0; st.n_set = 0; st.pad2 = 0;
+        if (hdr == S_OK && P.validate && !idset_dense(bound, len)) st.id_slots = (uint32_t)nb;
+        st.flags = flags;
+        P.ms[m] = st;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_prepass_scan(Params P)
 {
     __shared__ unsigned long long s_tiles[32], s_arena[32];
     __shared__ unsigned long long s_base_tiles, s_base_arena;
@@ -87,15 +117,7 @@ __global__ void __launch_bounds__(1024) k_prepass(Params P, int tile_words)
     for (int base = 0; base < P.n_modules; base += 1024) {
         int m = base + tid;
         unsigned long long nt = 0, nb = 0;
-        uint32_t hdr = S_OK, bound = 0, flags = 0;
-        if (m < P.n_modules) {
-            long long o = P.mod_off[m], len = P.mod_off[m + 1] - o;
-            if (len < 0 || len > 0x7fffffffLL) { hdr = S_CAPACITY; flags = MF_CAPACITY; len = 0; }
-            else hdr = header_status(P.words + o, len);
-            if (len >= 4) bound = P.words[o + 3];
-            nt = len > 0 ? (unsigned long long)((len + tile_words - 1) / tile_words) : 1;
-            if (hdr == S_OK && P.validate) nb = idset_words(bound, len);
-        }
+        if (m < P.n_modules) { nt = (unsigned long long)P.tile_off[m]; nb = (unsigned long long)P.abase[m]; }
         // block exclusive scan of (nt, nb)
         unsigned long long it = nt, ib = nb;
         for (int d = 1; d < 32; d <<= 1) {
@@ -118,21 +140,10 @@ __global__ void __launch_bounds__(1024) k_prepass(Params P, int tile_words)
         if (m < P.n_modules) {
             P.tile_off[m] = (int64_t)et;
             P.abase[m] = (int64_t)eb;
-            ModState s;
-            s.hdr = hdr; s.bound = bound; s.err_key = NO_KEY;
-            s.n_cap = s.n_mm = s.n_ep = s.n_fn = 0;
-            s.decl_lo = s.decl_hi = s.req_lo = s.req_hi = 0;
-            s.max_rid = 0;
-            s.arena_off = -1;
-            s.id_slots = 0; s.n_ids = 0; s.n_set = 0; s.pad2 = 0;
-            if (hdr == S_OK && P.validate && !idset_dense(bound, P.mod_off[m + 1] - P.mod_off[m]))
-                s.id_slots = (uint32_t)nb;
-            if (hdr == S_OK && P.validate) {
-                if ((long long)(eb + nb) <= P.arena_words) s.arena_off = (long long)eb;
-                else flags |= MF_NOARENA | MF_CAPACITY;
+            if (P.validate && P.ms[m].hdr == S_OK) {
+                if ((long long)(eb + nb) <= P.arena_words) P.ms[m].arena_off = (long long)eb;
+                else P.ms[m].flags |= MF_NOARENA | MF_CAPACITY;
             }
-            s.flags = flags;
-            P.ms[m] = s;
         }
         __syncthreads();
         if (tid == 1023) { s_base_tiles = et + nt; s_base_arena = eb + nb; }
@@ -1085,7 +1096,8 @@ extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint3
     P.out = out_words; P.validate = validate ? 1 : 0; P.recompute_bound = recompute_bound ? 1 : 0;
     P.max_spins = c.max_spins;
     P.stall_tile = c.stall_tile;
-    SPV_LAUNCH("k_prepass", st, k_prepass<<<1, 1024, 0, st>>>(P, c.T));
+    SPV_LAUNCH("k_prepass_mod", st, k_prepass_mod<<<sm_count() * 4, 256, 0, st>>>(P, c.T));
+    SPV_LAUNCH("k_prepass_scan", st, k_prepass_scan<<<1, 1024, 0, st>>>(P));
     int nsm = sm_count();
     SPV_LAUNCH("k_tile_setup", st, k_tile_setup<<<nsm * 4, 256, 0, st>>>(P));
     if (cudaPeekAtLastError() != cudaSuccess) return SPV_E_CUDA;
@@ -1148,7 +1160,8 @@ extern "C" int spv_validate_batch(const spv_batch *batch, const spv_table *table
     P.stall_tile = -1;
     int nsm = sm_count();
     int nb = (batch->n_modules + 255) / 256;
-    SPV_LAUNCH("k_prepass", st, k_prepass<<<1, 1024, 0, st>>>(P, c.T));
+    SPV_LAUNCH("k_prepass_mod", st, k_prepass_mod<<<sm_count() * 4, 256, 0, st>>>(P, c.T));
+    SPV_LAUNCH("k_prepass_scan", st, k_prepass_scan<<<1, 1024, 0, st>>>(P));
     SPV_LAUNCH("k_tile_setup", st, k_tile_setup<<<nsm * 4, 256, 0, st>>>(P));
     SPV_LAUNCH("k_table_framing", st, k_table_framing<<<nb, 256, 0, st>>>(P));
     SPV_LAUNCH("k_validate_rows", st, k_validate_rows<<<nsm * 8, 256, 0, st>>>(P));

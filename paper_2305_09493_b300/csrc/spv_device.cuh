@@ -131,10 +131,10 @@ __device__ __forceinline__ void spin_pause() { __nanosleep(32); }
 __device__ __forceinline__ uint32_t header_status(const uint32_t *w, long long n)
 {
     if (n < 5) return S_TRUNCATED;
-    if (w[0] != MAGIC) return S_BAD_MAGIC;
-    uint32_t v = w[1];
+    const uint32_t w0 = w[0], v = w[1], w4 = w[4];     // one round trip for the three words
+    if (w0 != MAGIC) return S_BAD_MAGIC;
     if ((v & 0xff0000ffu) != 0 || ((v >> 16) & 0xffu) != 1 || ((v >> 8) & 0xffu) > 6) return S_BAD_HEADER;
-    if (w[4] != 0) return S_BAD_HEADER;
+    if (w4 != 0) return S_BAD_HEADER;
     return S_OK;
 }
 

@@ -540,30 +540,47 @@ __device__ unsigned long long block_scan_modules(int n_mod, Val val, F f)
     return s_base;
 }
 
-__global__ void __launch_bounds__(1024) k_dis_prepass(DP P)
+// per module (many CTAs): header status, id-table form and size (parked in
+// arena_off until the scan), header bytes, first item
+__global__ void k_dis_premod(DP P)
+{
+    long long n_rows = P.first_row[P.n_mod];
+    if (n_rows > P.cap_rows) n_rows = P.cap_rows;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long mm = blockIdx.x * (long long)blockDim.x + threadIdx.x; mm < P.n_mod; mm += stride) {
+        const int m = (int)mm;
+        long long o = P.mod_off[m], len = P.mod_off[m + 1] - o;
+        uint32_t st = (len < 0 || len > 0x7fffffffLL) ? S_CAPACITY : header_status(P.words + o, len);
+        DisMod d;
+        d.bound = st == S_OK ? P.words[o + 3] : 0;
+        d.slots = (st == S_OK && !idtab_dense(d.bound, len)) ? (uint32_t)(len + 64) : 0;
+        d.arena_off = st == S_OK ? (long long)idtab_words(d.bound, len) : 0;
+        d.ok = st == S_OK;
+        d.status = st;
+        d.header_len = (st == S_OK && P.header) ? header_len(P.words + o) : 0;
+        d.named = 0;
+        long long fr = P.first_row[m];
+        d.item_base = (fr < n_rows ? fr : n_rows) + m;
+        P.dm[m] = d;
+    }
+}
+
+// one CTA: id-table offsets (exclusive prefix of the sizes); a module whose
+// table does not fit the arena gets no table and SPV_CAPACITY
+__global__ void __launch_bounds__(1024) k_dis_prescan(DP P)
 {
     long long n_rows = P.first_row[P.n_mod];
     if (n_rows > P.cap_rows) n_rows = P.cap_rows;
     unsigned long long used = block_scan_modules(P.n_mod,
-        [&](int m) -> unsigned long long {
-            long long o = P.mod_off[m], len = P.mod_off[m + 1] - o;
-            uint32_t st = (len < 0 || len > 0x7fffffffLL) ? S_CAPACITY : header_status(P.words + o, len);
-            return st == S_OK ? idtab_words(P.words[o + 3], len) : 0ull;
-        },
+        [&](int m) -> unsigned long long { return (unsigned long long)P.dm[m].arena_off; },
         [&](int m, unsigned long long excl, unsigned long long na) {
-            long long o = P.mod_off[m], len = P.mod_off[m + 1] - o;
-            uint32_t st = (len < 0 || len > 0x7fffffffLL) ? S_CAPACITY : header_status(P.words + o, len);
-            DisMod d;
-            d.bound = st == S_OK ? P.words[o + 3] : 0;
-            d.slots = (st == S_OK && !idtab_dense(d.bound, len)) ? (uint32_t)(len + 64) : 0;
+            DisMod &d = P.dm[m];
             d.arena_off = (long long)excl;
-            d.ok = st == S_OK && (long long)(excl + na) <= P.arena_words;
-            d.status = st != S_OK ? st : (d.ok ? S_OK : S_CAPACITY);
-            d.header_len = (d.ok && P.header) ? header_len(P.words + o) : 0;
-            d.named = 0;
-            long long fr = P.first_row[m];
-            d.item_base = (fr < n_rows ? fr : n_rows) + m;
-            P.dm[m] = d;
+            if (d.ok && (long long)(excl + na) > P.arena_words) {
+                d.ok = 0;
+                d.status = S_CAPACITY;
+                d.header_len = 0;
+            }
         });
     if (threadIdx.x == 0) {
         P.ctrl->arena_used = used < (unsigned long long)P.arena_words ? used : (unsigned long long)P.arena_words;
@@ -1103,7 +1120,8 @@ extern "C" int spv_disassemble_batch(const spv_batch *batch, const spv_table *ta
         if (dev < 64) { cached_nsm[dev] = nsm; cached_per_sm[dev] = per_sm; }
     }
     int nb = (batch->n_modules + 255) / 256;
-    SPV_LAUNCH("k_dis_prepass", st, k_dis_prepass<<<1, 1024, 0, st>>>(P));
+    SPV_LAUNCH("k_dis_premod", st, k_dis_premod<<<nsm * 4, 256, 0, st>>>(P));
+    SPV_LAUNCH("k_dis_prescan", st, k_dis_prescan<<<1, 1024, 0, st>>>(P));
     SPV_LAUNCH("k_dis_clear", st, k_dis_clear<<<nsm * 4, 256, 0, st>>>(P));
     SPV_LAUNCH("k_dis_ids", st, k_dis_ids<<<nsm * 8, 256, 0, st>>>(P));
     SPV_LAUNCH("k_dis_namelen", st, k_dis_namelen<<<nsm * 8, 256, 0, st>>>(P));
