@@ -612,29 +612,49 @@ __global__ void k_dis_clear(DP P)
 // first OpName per id and first definition per id (module-local rows)
 __global__ void k_dis_ids(DP P)
 {
+    // four rows per thread and step, all their loads issued before any
+    // update, so that a thread's rows do not wait on one another
+    constexpr int U = 4;
     const spvt::Tables &T = g_spv_tables;
-    long long n = (long long)P.ctrl->n_rows;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < n; row += stride) {
-        uint32_t m = P.mod[row];
-        const DisMod &md = P.dm[m];
-        if (!md.ok) continue;
-        uint32_t op = P.op[row], wc = P.wc[row];
-        uint32_t local = (uint32_t)(row - P.first_row[m]);
-        uint32_t *tab = P.arena + md.arena_off;
-        if (op == 5 && wc >= 2 && P.inline_names) {
-            uint32_t target = __ldg(P.words + P.off[row] + 1);
-            if (target < md.bound) {
-                if (!md.named) P.dm[m].named = 1;
-                atomicMin(&idtab_entry(tab, md.bound, md.slots, target, true)[0], local);
-                if (!md.slots) atomicAnd(&tab[3ull * md.bound + (target >> 5)], ~(1u << (target & 31)));
+    const long long n = (long long)P.ctrl->n_rows;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; r0 < n; r0 += U * stride) {
+        uint32_t mq[U], opq[U], wcq[U], ridq[U];
+        #pragma unroll
+        for (int q = 0; q < U; q++) {
+            const long long row = r0 + q * stride;
+            mq[q] = ~0u; opq[q] = 0; wcq[q] = 0; ridq[q] = 0;
+            if (row < n) { mq[q] = P.mod[row]; opq[q] = P.op[row]; wcq[q] = P.wc[row]; ridq[q] = P.rid[row]; }
+        }
+        uint32_t okq[U], boundq[U], slotsq[U], namedq[U];
+        long long aoq[U], frq[U];
+        #pragma unroll
+        for (int q = 0; q < U; q++) {
+            okq[q] = 0; boundq[q] = 0; slotsq[q] = 0; namedq[q] = 0; aoq[q] = 0; frq[q] = 0;
+            if (mq[q] != ~0u) {
+                const DisMod &md = P.dm[mq[q]];
+                okq[q] = md.ok; boundq[q] = md.bound; slotsq[q] = md.slots; namedq[q] = md.named;
+                aoq[q] = md.arena_off; frq[q] = P.first_row[mq[q]];
             }
         }
-        if (op < 256 && (T.ops[op].flags & 4)) {
-            uint32_t q = 1 + ((T.ops[op].flags >> 1) & 1);
-            if (q < wc) {
-                uint32_t id = P.rid[row];
-                if (id < md.bound) atomicMin(&idtab_entry(tab, md.bound, md.slots, id, true)[2], local);
+        #pragma unroll
+        for (int q = 0; q < U; q++) {
+            if (!okq[q]) continue;
+            const long long row = r0 + q * stride;
+            const uint32_t m = mq[q], op = opq[q], wc = wcq[q], bound = boundq[q], slots = slotsq[q];
+            const uint32_t local = (uint32_t)(row - frq[q]);
+            uint32_t *tab = P.arena + aoq[q];
+            if (op == 5 && wc >= 2 && P.inline_names) {
+                uint32_t target = __ldg(P.words + P.off[row] + 1);
+                if (target < bound) {
+                    if (!namedq[q]) P.dm[m].named = 1;
+                    atomicMin(&idtab_entry(tab, bound, slots, target, true)[0], local);
+                    if (!slots) atomicAnd(&tab[3ull * bound + (target >> 5)], ~(1u << (target & 31)));
+                }
+            }
+            if (op < 256 && (T.ops[op].flags & 4)) {
+                uint32_t qq = 1 + ((T.ops[op].flags >> 1) & 1);
+                if (qq < wc && ridq[q] < bound) atomicMin(&idtab_entry(tab, bound, slots, ridq[q], true)[2], local);
             }
         }
     }
@@ -645,28 +665,41 @@ __global__ void k_dis_ids(DP P)
 __global__ void k_dis_namelen(DP P)
 {
     if (!P.inline_names) return;
+    // the op column is scanned eight rows per thread and step (loads issued
+    // together); the few OpName rows do the work
+    constexpr int U = 8;
     long long n = (long long)P.ctrl->n_rows;
     long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < n; row += stride) {
-        if (P.op[row] != 5) continue;
-        uint32_t wc = P.wc[row];
-        if (wc < 2) continue;
-        uint32_t m = P.mod[row];
-        const DisMod &md = P.dm[m];
-        if (!md.ok) continue;
-        const uint32_t *iw = P.words + P.off[row];
-        uint32_t target = __ldg(iw + 1);
-        if (target >= md.bound) continue;
-        uint32_t *e = idtab_entry(P.arena + md.arena_off, md.bound, md.slots, target, false);
-        if (!e || e[0] != (uint32_t)(row - P.first_row[m])) continue;
-        uint32_t len = 0;
-        for (uint32_t i = 2; i < wc; i++) {
-            uint32_t v = __ldg(iw + i);
-            uint32_t z = (v - 0x01010101u) & ~v & 0x80808080u;
-            if (z) { len += (uint32_t)((__ffs(z) - 1) >> 3); break; }
-            len += 4;
+    for (long long r0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; r0 < n; r0 += U * stride) {
+        uint32_t hit = 0;
+        #pragma unroll
+        for (int q = 0; q < U; q++) {
+            const long long row = r0 + q * stride;
+            if (row < n && P.op[row] == 5) hit |= 1u << q;
         }
-        e[1] = len;
+        while (hit) {
+            const int q = __ffs(hit) - 1;
+            hit &= hit - 1;
+            const long long row = r0 + q * stride;
+            uint32_t wc = P.wc[row];
+            if (wc < 2) continue;
+            uint32_t m = P.mod[row];
+            const DisMod &md = P.dm[m];
+            if (!md.ok) continue;
+            const uint32_t *iw = P.words + P.off[row];
+            uint32_t target = __ldg(iw + 1);
+            if (target >= md.bound) continue;
+            uint32_t *e = idtab_entry(P.arena + md.arena_off, md.bound, md.slots, target, false);
+            if (!e || e[0] != (uint32_t)(row - P.first_row[m])) continue;
+            uint32_t len = 0;
+            for (uint32_t i = 2; i < wc; i++) {
+                uint32_t v = __ldg(iw + i);
+                uint32_t z = (v - 0x01010101u) & ~v & 0x80808080u;
+                if (z) { len += (uint32_t)((__ffs(z) - 1) >> 3); break; }
+                len += 4;
+            }
+            e[1] = len;
+        }
     }
 }
 
