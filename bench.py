@@ -165,58 +165,32 @@ def issue_roofline(warp_inst, ms, clk):
 
 def serve_leg(spvgpu, w_np, off_np, rate, seconds, max_batch_modules=0, pool_size=2000, cap=4 << 30):
     """Poisson arrivals at `rate` modules/s for `seconds`, modules drawn in
-    turn from the batch workload (its size distribution). Latency: from each
-    module's scheduled arrival to its completion (library clock), so time a
-    module waited to be admitted counts too."""
+    turn from the batch workload (its size distribution), replayed by the
+    library's native load thread (spv_serve_replay: each module submitted at
+    its scheduled time, retried while admission refuses it, collected in
+    order). Latency is reported from each module's scheduled arrival to its
+    completion (library clock), so time spent waiting for admission counts,
+    and from submission to completion (the server alone)."""
     m_total = len(off_np) - 1
     pool = [np.ascontiguousarray(w_np[off_np[i]:off_np[i + 1]]) for i in range(min(pool_size, m_total))]
     srv = spvgpu.Server(hbm_cap_bytes=cap, max_batch_modules=max_batch_modules)
-    # warm up the server's kernels
-    for m in pool[:8]:
-        t = srv.submit(m)
-        srv.wait(t)
-        srv.release(t)
+    srv.replay(pool[:8], np.arange(8, dtype=np.int64) * 1000)        # warm up the server's kernels
     rng = np.random.default_rng(12345)
     n = max(1, int(rate * seconds))
-    arrive = np.cumsum(rng.exponential(1.0 / rate, n))
-    lat, batch_sizes = [], []
-    words_done = 0
-    busy = 0
-    pending = []
-    head = 0
-    i = 0
-    t0 = time.monotonic_ns()
-    while i < n or head < len(pending):
-        now = time.monotonic_ns() - t0
-        while i < n and arrive[i] * 1e9 <= now:
-            m = pool[i % len(pool)]
-            t = srv.submit(m)
-            if t is None:
-                busy += 1
-                break
-            pending.append((t, t0 + int(arrive[i] * 1e9), len(m)))
-            i += 1
-        progressed = False
-        while head < len(pending):
-            t, a, nw = pending[head]
-            r = srv.poll(t)
-            if r is None:
-                break
-            lat.append(r.done_ns - a)
-            batch_sizes.append(r.batch_modules)
-            words_done += nw
-            srv.release(t)
-            head += 1
-            progressed = True
-        if not progressed:
-            time.sleep(0)
-    elapsed = (time.monotonic_ns() - t0) / 1e9
+    arrive_ns = (np.cumsum(rng.exponential(1.0 / rate, n)) * 1e9).astype(np.int64)
+    mods = [pool[i % len(pool)] for i in range(n)]
+    t0 = time.monotonic()
+    lat, srv_ns, bm, busy = srv.replay(mods, arrive_ns)
+    elapsed = time.monotonic() - t0
     srv.close()
-    lat_ms = np.array(lat) / 1e6
+    words_done = sum(len(m) for m in mods)
+    lat_ms, srv_ms = lat / 1e6, srv_ns / 1e6
     return {"rate_per_s": rate, "seconds": seconds, "modules": n, "p50_ms": float(np.percentile(lat_ms, 50)),
-            "p99_ms": float(np.percentile(lat_ms, 99)), "mean_batch_modules": float(np.mean(batch_sizes)),
+            "p99_ms": float(np.percentile(lat_ms, 99)),
+            "server_p50_ms": float(np.percentile(srv_ms, 50)), "server_p99_ms": float(np.percentile(srv_ms, 99)),
+            "mean_batch_modules": float(np.mean(bm)),
             "throughput_modules_per_s": n / elapsed, "gbs": 4 * words_done / elapsed / 1e9,
-            "admission_retries": busy}
+            "admission_retries": int(busy)}
 
 
 def cpu_baseline(words, mod_off, budget_s=12.0):

@@ -303,6 +303,20 @@ int spv_serve_wait(spv_server *s, uint64_t ticket, spv_result *out, int64_t time
 int spv_serve_release(spv_server *s, uint64_t ticket);
 /* Stop the scheduler, wait for in-flight batches, free everything. */
 void spv_serve_destroy(spv_server *s);
+/*
+ * Load replay, for measuring the server under an arrival process: module i
+ * (mods[i], n_words[i] words in host memory) is submitted arrive_ns[i]
+ * nanoseconds (non-decreasing) after the start, from a native thread,
+ * retrying while admission says SPV_E_BUSY; the calling thread waits for the
+ * modules in order and releases them. Per module (host arrays of n):
+ * latency_ns from its scheduled arrival to its completion, and optionally
+ * server_ns from submission to completion and batch_modules; busy_retries
+ * (optional) counts the refused submissions. Returns SPV_SUCCESS, SPV_E_ARG,
+ * or the first failing call's code.
+ */
+int spv_serve_replay(spv_server *s, int32_t n, const uint32_t *const *mods, const int64_t *n_words,
+                     const int64_t *arrive_ns, int64_t *latency_ns, int64_t *server_ns, uint32_t *batch_modules,
+                     int64_t *busy_retries);
 
 /*
  * Host-resident batches, transfers overlapped with the kernels (a library

@@ -494,3 +494,55 @@ extern "C" void spv_serve_destroy(spv_server *s)
     cudaFreeHost(s->hpool);
     delete s;
 }
+
+// Load replay: modules submitted at scheduled times from a native thread,
+// collected in order by the calling thread. Measures the server under a
+// given arrival process without the caller's own submission costs in the
+// way.
+extern "C" int spv_serve_replay(spv_server *s, int32_t n, const uint32_t *const *mods, const int64_t *n_words,
+                                const int64_t *arrive_ns, int64_t *latency_ns, int64_t *server_ns,
+                                uint32_t *batch_modules, int64_t *busy_retries)
+{
+    if (!s || n < 0 || (n && (!mods || !n_words || !arrive_ns || !latency_ns))) return SPV_E_ARG;
+    for (int32_t i = 0; i < n; i++)
+        if (arrive_ns[i] < 0 || (i && arrive_ns[i] < arrive_ns[i - 1]) || n_words[i] < 0) return SPV_E_ARG;
+    std::vector<uint64_t> tickets((size_t)n);
+    std::atomic<int32_t> submitted{0};
+    std::atomic<int> failed{0};
+    std::atomic<int64_t> busy{0};
+    const uint64_t t0 = now_ns() + 1000000;         // start 1 ms from now
+    std::thread sub([&] {
+        for (int32_t i = 0; i < n; i++) {
+            const uint64_t target = t0 + (uint64_t)arrive_ns[i];
+            for (;;) {
+                const uint64_t now = now_ns();
+                if (now >= target) break;
+                if (target - now > 200000) std::this_thread::sleep_for(std::chrono::nanoseconds(target - now - 100000));
+            }
+            for (;;) {
+                const int rc = spv_serve_submit(s, mods[i], n_words[i], &tickets[(size_t)i]);
+                if (rc == SPV_SUCCESS) break;
+                if (rc != SPV_E_BUSY) { failed.store(rc); submitted.store(n + 1, std::memory_order_release); return; }
+                busy.fetch_add(1);
+                std::this_thread::sleep_for(std::chrono::microseconds(10));
+            }
+            submitted.store(i + 1, std::memory_order_release);
+        }
+    });
+    int rc = SPV_SUCCESS;
+    for (int32_t i = 0; i < n && rc == SPV_SUCCESS; i++) {
+        int32_t got;
+        while ((got = submitted.load(std::memory_order_acquire)) <= i) std::this_thread::yield();
+        if (got > n) { rc = failed.load(); break; }
+        spv_result r{};
+        const int w = spv_serve_wait(s, tickets[(size_t)i], &r, 60000000);
+        if (w != 1) { rc = w < 0 ? w : SPV_E_CUDA; break; }
+        latency_ns[i] = (int64_t)(r.done_ns - (t0 + (uint64_t)arrive_ns[i]));
+        if (server_ns) server_ns[i] = (int64_t)(r.done_ns - r.submit_ns);
+        if (batch_modules) batch_modules[i] = r.batch_modules;
+        spv_serve_release(s, tickets[(size_t)i]);
+    }
+    sub.join();
+    if (busy_retries) *busy_retries = busy.load();
+    return rc;
+}

@@ -16,6 +16,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -205,7 +206,6 @@ class Table:
 
     def to_numpy(self, n_rows=None):
         """Host copy with the table's own unsigned dtypes."""
-        import numpy as np
         if n_rows is None:
             n_rows = int(self.mod_first_row[-1].item())
         n = min(n_rows, self.capacity_rows)
@@ -380,6 +380,8 @@ def _serve_lib():
         lib.spv_serve_release.argtypes = [P, ctypes.c_uint64]
         lib.spv_serve_destroy.restype = None
         lib.spv_serve_destroy.argtypes = [P]
+        lib.spv_serve_replay.restype = ctypes.c_int
+        lib.spv_serve_replay.argtypes = [P, ctypes.c_int32, P, P, P, P, P, P, P]
         lib._serve_ready = True
     return lib
 
@@ -441,6 +443,25 @@ class Server:
         if rc < 0:
             raise SpvError(f"spv_serve_wait failed with code {rc}")
         return r if rc == 1 else None
+
+    def replay(self, modules, arrive_ns):
+        """Submit modules[i] (contiguous uint32 numpy arrays) arrive_ns[i]
+        nanoseconds after the start from a native thread and collect them in
+        order. Returns (latency_ns from arrival, server_ns from submission,
+        batch_modules, busy_retries)."""
+        n = len(modules)
+        ptrs = (ctypes.c_void_p * max(1, n))(*[m.ctypes.data for m in modules])
+        nw = np.array([len(m) for m in modules], np.int64)
+        arr = np.ascontiguousarray(arrive_ns, np.int64)
+        lat = np.zeros(n, np.int64)
+        srv_ns = np.zeros(n, np.int64)
+        bm = np.zeros(n, np.uint32)
+        busy = ctypes.c_int64(0)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        rc = _serve_lib().spv_serve_replay(self.h, n, ctypes.cast(ptrs, ctypes.c_void_p), p(nw), p(arr), p(lat),
+                                           p(srv_ns), p(bm), ctypes.byref(busy))
+        _check(rc, "spv_serve_replay")
+        return lat, srv_ns, bm, busy.value
 
     @staticmethod
     def text_of(r):

@@ -133,3 +133,25 @@ def test_poll_and_latency_stamps(gpu):
             srv.release(t)
     finally:
         srv.close()
+
+
+def test_replay_reports_every_module(gpu):
+    """spv_serve_replay submits on its own thread at the scheduled times and
+    collects in order: every module gets a latency no shorter than its time
+    in the server, batches form under load, and the server stays usable."""
+    mods = _modules(60, 21)
+    srv = gpu.Server(hbm_cap_bytes=1 << 30)
+    try:
+        arrive = (np.arange(60, dtype=np.int64) * 20_000)        # one module every 20 us
+        lat, srv_ns, bm, busy = srv.replay(mods, arrive)
+        assert (srv_ns > 0).all() and (lat >= srv_ns - 1_000_000).all()
+        assert bm.max() >= 1 and busy >= 0
+        t = srv.submit(mods[0])
+        r = srv.wait(t)
+        st, er, text, _ = _expected(mods[0])
+        assert (r.status, r.err_row, gpu.Server.text_of(r)) == (st, er, text)
+        srv.release(t)
+        with pytest.raises(Exception):
+            srv.replay(mods[:3], np.array([5, 3, 9], np.int64))  # arrivals must not decrease
+    finally:
+        srv.close()
