@@ -316,10 +316,10 @@ def main():
     tj = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tj):
         t = json.load(open(tj))
-        if (t.get("kernel") == kname and t.get("source_sha") == source_hash(kname) and t.get("workload") == args.workload
-                and t.get("modules") == M):
-            traffic = t.get("bytes_per_launch")
-            warp_inst = t.get("warp_instructions_per_launch")
+        kt = t.get("kernels", {}).get(kname, {})
+        if kt.get("source_sha") == source_hash(kname) and t.get("workload") == args.workload and t.get("modules") == M:
+            traffic = kt.get("bytes_per_launch")
+            warp_inst = kt.get("warp_instructions_per_launch")
     kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in
                sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
