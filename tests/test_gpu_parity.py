@@ -328,6 +328,33 @@ def test_text_buffer_at_any_alignment(gpu):
         assert np.array_equal(toff.cpu().numpy(), woff)
 
 
+def test_thousands_of_tiny_modules(gpu):
+    """Tiles that span thousands of modules: a batch of mostly 5-word (header
+    only) and minimal modules, with truncated and bad-magic ones and a few
+    normal ones mixed in, so that a disassembly tile of 2,048 items holds
+    thousands of module headers and the per-tile module lookup runs at its
+    maximum."""
+    rng = np.random.default_rng(29)
+    base = H.minimal_body()
+    mods = []
+    for i in range(7000):
+        kind = int(rng.integers(0, 10))
+        if kind < 5:
+            mods.append(H.module([], bound=1))                  # header only
+        elif kind < 8:
+            mods.append(H.module(base, bound=8))
+        elif kind == 8:
+            mods.append(H.module(base, bound=8)[:int(rng.integers(0, 12))])  # truncated, possibly empty
+        else:
+            x = H.module(base, bound=8).copy(); x[0] = 0x12345678; mods.append(x)
+    n_instr, n_k = synth.batch_shape(3, 5, median=1500, lo=200, hi=3000)
+    w3, off3 = synth.batch(n_instr, n_k, 5)
+    for i in range(3):
+        mods.insert(1000 * (i + 1), w3[off3[i]:off3[i + 1]])
+    words, offs = H.batch(mods)
+    check(gpu, words, offs, dis=True)
+
+
 def test_bounded_wait_times_out_without_hanging(gpu):
     w, off, _, _ = synth.large_module(6, n_instr=60_000, n_funcs=4)
     cfg = gpu.make_config(tile_words=1024, threads=128, max_spins=2000, test_stall_tile=5)
