@@ -32,13 +32,13 @@ namespace {
 
 constexpr uint32_t NOROW = 0xFFFFFFFFu;
 #ifndef SPV_DIS_NT
-#define SPV_DIS_NT 512
+#define SPV_DIS_NT 768
 #endif
 #ifndef SPV_DIS_IPT
-#define SPV_DIS_IPT 4
+#define SPV_DIS_IPT 3
 #endif
 #ifndef SPV_DIS_TEXT_KB
-#define SPV_DIS_TEXT_KB 80
+#define SPV_DIS_TEXT_KB 88
 #endif
 #ifndef SPV_DIS_MIN_BLOCKS
 #define SPV_DIS_MIN_BLOCKS 1
@@ -48,7 +48,7 @@ constexpr int IPT = SPV_DIS_IPT;                  // items per thread
 constexpr int ITEMS = DNT * IPT;                  // items per tile
 constexpr int TEXT_SMEM = SPV_DIS_TEXT_KB * 1024; // shared text buffer per tile
 #ifndef SPV_DIS_STAGE_WORDS
-#define SPV_DIS_STAGE_WORDS 10240
+#define SPV_DIS_STAGE_WORDS 12288
 #endif
 constexpr int STAGE_WORDS = SPV_DIS_STAGE_WORDS;  // a tile's instruction words staged in shared memory
 constexpr uint32_t NOSTAGE = 0xFFFFFFFFu;
