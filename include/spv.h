@@ -204,10 +204,17 @@ int spv_encode_batch(const spv_batch *src, const spv_table *table, uint32_t *out
 
 /* Disassembly options (Listing 10): inline_names prints ids as
  * %<name>_<id> using each id's first OpName; header prints the five header
- * fields as comment lines first. */
+ * fields as comment lines first. max_spins bounds every wait of the text
+ * offset look-back (0: 1 << 20 polls); a wait that runs out ends the call
+ * with SPV_TIMEOUT in dis_status for every module (the text is then not
+ * complete). test_stall_tile is a test hook, 0 = off: with n > 0, text tile
+ * n-1 never publishes its byte count, so the waits of the tiles after it run
+ * out. Zero-initialised fields take the defaults. */
 typedef struct spv_dis_opts {
     int32_t inline_names;
     int32_t header;
+    int64_t max_spins;
+    int64_t test_stall_tile;
 } spv_dis_opts;
 
 /* Workspace bytes for spv_disassemble_batch. arena_words is the capacity,

@@ -86,6 +86,7 @@ struct DP {
     unsigned long long *tstate;
     int *tile_m0;            // per tile of k_dis_main: the module holding its first item
     long long max_spins;
+    long long stall_tile;    // test hook: this tile never publishes its look-back state (-1: none)
 };
 
 // ---------------------------------------------------------------------------
@@ -788,7 +789,7 @@ __device__ void dis_lookback(const DP &P, MainSmem &s, long long t, uint32_t tot
             hi -= 32;
         }
         if (gave_up && lane == 0) { atomicExch(&P.ctrl->timeout, 1u); s.gave_up = 1; }
-        if (lane == 0) st_release(&P.tstate[t], F_INC | (excl + total));
+        if (lane == 0 && t != P.stall_tile) st_release(&P.tstate[t], F_INC | (excl + total));
     }
     if (lane == 0) {
         s.base = excl;
@@ -985,7 +986,7 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
         #pragma unroll
         for (int w = 0; w < DNT / 32; w++) total += s.warp_tot[w];
         // the tile's byte count, published before any wait of this tile
-        if (tid == 0) st_release(&P.tstate[t], (t == 0 ? F_INC : F_AGG) | total);
+        if (tid == 0 && t != P.stall_tile) st_release(&P.tstate[t], (t == 0 ? F_INC : F_AGG) | total);
         const bool last_tile = i0 + ITEMS >= n_items;
         const bool staged = total <= (uint32_t)TEXT_SMEM;
         auto format_item = [&](auto &k, int j) {
@@ -1135,7 +1136,8 @@ extern "C" int spv_disassemble_batch(const spv_batch *batch, const spv_table *ta
     P.tstate = (unsigned long long *)(w + L.tstate);
     P.tile_m0 = (int *)(w + L.tile_m0);
     P.arena = (uint32_t *)(w + L.arena); P.arena_words = L.arena_words;
-    P.max_spins = 1LL << 20;
+    P.max_spins = opts && opts->max_spins > 0 ? opts->max_spins : 1LL << 20;
+    P.stall_tile = opts && opts->test_stall_tile > 0 ? opts->test_stall_tile - 1 : -1;
     // device properties and occupancy, once per device
     static int cached_nsm[64] = {}, cached_per_sm[64] = {};
     int dev = 0;

@@ -47,7 +47,8 @@ class SpvConfig(ctypes.Structure):
 
 
 class SpvDisOpts(ctypes.Structure):
-    _fields_ = [("inline_names", ctypes.c_int32), ("header", ctypes.c_int32)]
+    _fields_ = [("inline_names", ctypes.c_int32), ("header", ctypes.c_int32), ("max_spins", ctypes.c_int64),
+                ("test_stall_tile", ctypes.c_int64)]
 
 
 class SpvError(RuntimeError):
@@ -294,7 +295,7 @@ class DisWorkspace:
 
 
 def disassemble(words, mod_off, table, *, inline_names=True, header=True, text=None, workspace=None, stream=None,
-                arena_words=0, sync=True):
+                arena_words=0, sync=True, max_spins=0, test_stall_tile=0):
     """Text of every module. With sync (default) the call waits for the
     stream, grows the text buffer if needed, and returns
     (text uint8 tensor trimmed to its size, text_off int64 tensor, dis_status)."""
@@ -306,7 +307,7 @@ def disassemble(words, mod_off, table, *, inline_names=True, header=True, text=N
     dis_status = torch.empty(max(1, m), dtype=torch.int32, device=dev)
     if text is None:
         text = torch.empty(max(1, 8 * words.numel()), dtype=torch.uint8, device=dev)
-    opts = SpvDisOpts(1 if inline_names else 0, 1 if header else 0)
+    opts = SpvDisOpts(1 if inline_names else 0, 1 if header else 0, max_spins, test_stall_tile)
     for _ in range(2):
         rc = spv_disassemble_batch(batch_of(words, mod_off), table.c(), opts, _ptr(text), text.numel(),
                                    _ptr(text_off), _ptr(dis_status), _ptr(workspace.buf), workspace.bytes,

@@ -364,6 +364,19 @@ def test_bounded_wait_times_out_without_hanging(gpu):
     check(gpu, w, off)
 
 
+def test_text_lookback_times_out_without_hanging(gpu):
+    """A text tile that never publishes its byte count (the test hook): the
+    look-backs of the tiles after it give up after max_spins polls, every
+    module reports TIMEOUT, and the next call on the same context is exact."""
+    n_instr, n_k = synth.batch_shape(20, 41, median=1500, lo=1000, hi=3000)
+    w, off = synth.batch(n_instr, n_k, 41)                  # about 30,000 rows: several text tiles
+    g = run(gpu, w, off)
+    _, _, dst = gpu.disassemble(g["_w"], g["_o"], g["_r"]["table"], sync=False, max_spins=2000, test_stall_tile=2)
+    torch.cuda.synchronize()
+    assert all(gpu.STATUS[int(x)] == "TIMEOUT" for x in dst.cpu().numpy())
+    check_dis(gpu, w, off, g, modes=((True, True),))
+
+
 # ---------------------------------------------------------------------------
 # full-size workloads
 # ---------------------------------------------------------------------------
