@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="batch", choices=["batch", "large", "single"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "large", "single", "bins"],
+                    help="bins: 4 size bins x 1,000 modules, tile-shape sweep and autotuned CUDA-graph replay per bin")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-per-module", action="store_true", help="skip the per-module comparison leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -239,10 +240,118 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+BIN_INSTR = (200, 2_000, 20_000, 50_000)
+
+
+def run_bins(args):
+    """Size bins (1,000 modules each at 200 / 2k / 20k / 50k instructions, 1-8
+    kernels): per bin every tile shape of spv_process_batch timed, the
+    autotuner's pick, and the whole step (decode + validate + encode with the
+    picked shape, then disassemble) captured once in a CUDA graph and
+    replayed; against the same decode + validate + encode with one launch
+    sequence per module."""
+    import torch
+    from paper_2305_09493_b300 import build, spvgpu, synth
+    build.build()
+    spvgpu.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    bins, tot_words, tot_ms = [], 0, 0.0
+    clocks = Clocks(torch.cuda.current_device())
+    launches = 0
+    for b, ni in enumerate(BIN_INSTR):
+        rng = np.random.default_rng(100 + b)
+        n_instr = np.full(1000, ni, np.int64)
+        n_k = rng.integers(1, 9, 1000).astype(np.int32)
+        w_np, off_np = synth.batch(n_instr, n_k, 1_000_000 * (b + 1))
+        W, M = len(w_np), len(off_np) - 1
+        words = torch.from_numpy(w_np.view(np.int32)).to(dev)
+        mod_off = torch.from_numpy(off_np).to(dev)
+        table = spvgpu.Table(M, W, dev)
+        out = torch.empty_like(words)
+        sweep = {}
+        for tw, nt in spvgpu.TILE_SHAPES:
+            c = spvgpu.make_config(tw, nt)
+            ws = spvgpu.Workspace(M, W, dev, 0, c)
+            for _ in range(2):
+                spvgpu.process(words, mod_off, encode=True, table=table, workspace=ws, out=out, cfg=c)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t = 0.0
+            for _ in range(3):
+                flush.zero_()
+                e0.record()
+                spvgpu.process(words, mod_off, encode=True, table=table, workspace=ws, out=out, cfg=c)
+                e1.record()
+                torch.cuda.synchronize()
+                t += e0.elapsed_time(e1)
+            sweep[f"{tw}x{nt}"] = t / 3
+        best, best_ms, _ = spvgpu.autotune(words, mod_off, table=table, out=out, reps=3)
+        ws = spvgpu.Workspace(M, W, dev, 0, best)
+        dws = spvgpu.DisWorkspace(M, W, W, dev)
+        _, toff, _ = spvgpu.disassemble(words, mod_off, table, workspace=dws)
+        L = int(toff[-1].item())
+        text = torch.empty(L + 16, dtype=torch.uint8, device=dev)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            spvgpu.process(words, mod_off, encode=True, table=table, workspace=ws, out=out, cfg=best)
+            spvgpu.disassemble(words, mod_off, table, workspace=dws, text=text, sync=False)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            r = spvgpu.process(words, mod_off, encode=True, table=table, workspace=ws, out=out, cfg=best)
+            _, _, dst = spvgpu.disassemble(words, mod_off, table, workspace=dws, text=text, sync=False)
+        for _ in range(max(3, args.warmup)):
+            g.replay()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        step_ms = float(np.median(ts))
+        ok = bool((r["status"] == 0).all().item()) and bool((dst == 0).all().item())
+        # decode + validate + encode, one launch sequence per module
+        pm = spvgpu.make_config(per_module=1)
+        wsp = spvgpu.Workspace(M, W, dev, 0, pm)
+        spvgpu.process(words, mod_off, encode=True, table=table, workspace=wsp, out=out, cfg=pm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        spvgpu.process(words, mod_off, encode=True, table=table, workspace=wsp, out=out, cfg=pm)
+        torch.cuda.synchronize()
+        pm_ms = (time.perf_counter() - t0) * 1e3
+        launches += args.steps * 14
+        bins.append({"instr_per_module": ni, "modules": M, "words": W, "text_bytes": L,
+                     "sweep_process_ms": {k: round(v, 4) for k, v in sweep.items()},
+                     "autotuned": f"{best.tile_words}x{best.threads}", "autotuned_process_ms": best_ms,
+                     "step_ms": step_ms, "gbs": 4 * W / (step_ms * 1e-3) / 1e9,
+                     "process_gbs": 4 * W / (best_ms * 1e-3) / 1e9,
+                     "per_module_process_gbs": 4 * W / (pm_ms * 1e-3) / 1e9, "all_status_ok": ok})
+        tot_words += W
+        tot_ms += step_ms
+        del words, mod_off, table, out, ws, wsp, dws, text, g, r, dst
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": 4 * tot_words / (tot_ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "4 size bins x 1,000 modules at 200 / 2k / 20k / 50k instructions",
+                       "parallelism": "1 GPU", "graph": "each bin's step captured once in a CUDA graph, replayed",
+                       "l2": "L2 flushed (252 MiB write) before every timed replay"},
+            "bins": bins, "clocks": clk, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "bins":
+        run_bins(args)
         return
     import torch
     rank, world = dist_setup(args.gpus)

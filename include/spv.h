@@ -103,9 +103,11 @@ typedef struct spv_table {
 
 /* Tuning of the batched kernels; zero fields take defaults. */
 typedef struct spv_config {
-    int32_t tile_words;         /* words per tile: 1024, 2048, 4096 or 8192 (default 4096) */
-    int32_t threads;            /* threads per CTA: 128, 256 or 512 (default 256); tile_words/threads must be 8
-                                   or 16, and 512 threads only with 16 */
+    int32_t tile_words;         /* words per tile: 1024, 2048, 4096 or 8192 */
+    int32_t threads;            /* threads per CTA: 128, 256 or 512; tile_words/threads must be 8 or 16, and
+                                   512 threads only with 16. Both 0 (default): 2048 x 128 for batches whose
+                                   mean module is under 4,096 words, else 4096 x 256; one of them 0: that one
+                                   takes its default (4096 words, 256 threads) */
     int32_t ctas_per_sm;        /* resident CTAs per SM for the persistent grid (default: occupancy maximum) */
     int32_t per_module;         /* 1: one launch sequence per module instead of one persistent launch
                                    (comparison path; copies mod_off to the host and synchronises) */
@@ -175,6 +177,21 @@ int spv_process_batch(const spv_batch *batch, spv_table *table, uint32_t *status
 int spv_process_batch_noalloc(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row,
                               int validate, uint32_t *out_words, int recompute_bound,
                               const spv_config *cfg, spv_stream_t stream);
+
+/*
+ * spv_autotune_batch -- pick the fastest tile shape (tile_words x threads)
+ * of spv_process_batch for a batch (a library service; the paper has no
+ * counterpart). Runs the batch once to warm up and reps times (0: 3) timed
+ * with CUDA events on the stream for every built shape whose workspace fits
+ * in workspace_bytes, then once more with the fastest, so the outputs are
+ * that shape's; arguments as spv_process_batch (recompute_bound = 1).
+ * Writes *best (tile_words, threads; other fields 0) and *best_ms (mean
+ * time of one call). Synchronises the stream; not for use under stream
+ * capture. SPV_E_WORKSPACE when no shape fits.
+ */
+int spv_autotune_batch(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row, int validate,
+                       uint32_t *out_words, void *workspace, size_t workspace_bytes, int reps, spv_config *best,
+                       float *best_ms, spv_stream_t stream);
 
 /* spv_decode_batch -- spv_process_batch with validate = 0 and no encode. */
 int spv_decode_batch(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row,

@@ -954,9 +954,15 @@ Layout make_layout(int n_mod, long long n_words, long long arena_words, int tile
 
 struct Cfg { int T, NT, L, ctas_per_sm, per_module; long long max_spins, stall_tile; };
 
-int resolve_cfg(const spv_config *c, Cfg *out)
+// A tile shape left unset (tile_words and threads both 0) follows the batch:
+// batches of small modules (mean under 4,096 words) take 2,048-word tiles
+// of 128 threads, others 4,096-word tiles of 256 threads (measured on
+// 1,000-module bins of 200 to 50,000 instructions).
+int resolve_cfg(const spv_config *c, Cfg *out, int n_modules, long long n_words)
 {
     Cfg r{4096, 256, 16, 0, 0, 1LL << 20, -1};
+    const bool auto_shape = !c || (!c->tile_words && !c->threads);
+    if (auto_shape && n_modules > 0 && n_words / n_modules < 4096) { r.T = 2048; r.NT = 128; }
     if (c) {
         if (c->tile_words) r.T = c->tile_words;
         if (c->threads) r.NT = c->threads;
@@ -1070,7 +1076,7 @@ int sm_count()
 extern "C" size_t spv_workspace_bytes(int32_t n_modules, int64_t n_words, int64_t arena_words, const spv_config *cfg)
 {
     Cfg c;
-    if (n_modules < 0 || n_words < 0 || resolve_cfg(cfg, &c)) return 0;
+    if (n_modules < 0 || n_words < 0 || resolve_cfg(cfg, &c, n_modules, n_words)) return 0;
     return make_layout(n_modules, n_words, arena_words, c.T).total;
 }
 
@@ -1080,7 +1086,8 @@ extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint3
                                  spv_stream_t stream)
 {
     Cfg c;
-    if (!check_batch(batch) || !table || !status || !err_row || resolve_cfg(cfg, &c)) return SPV_E_ARG;
+    if (!check_batch(batch) || !table || !status || !err_row || resolve_cfg(cfg, &c, batch->n_modules, batch->n_words))
+        return SPV_E_ARG;
     if (!table->op || !table->wc || !table->off || !table->rtype || !table->rid || !table->mod ||
         !table->mod_first_row || !table->mod_n_instr || table->capacity_rows < 0)
         return SPV_E_ARG;
@@ -1129,6 +1136,54 @@ extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint3
     return cudaPeekAtLastError() == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;
 }
 
+// The tile shapes k_tile is built for, tried by the autotuner.
+static const int kTileShapes[][2] = {{4096, 256}, {8192, 512}, {2048, 256}, {2048, 128}, {1024, 128}};
+
+extern "C" int spv_autotune_batch(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row,
+                                  int validate, uint32_t *out_words, void *workspace, size_t workspace_bytes,
+                                  int reps, spv_config *best, float *best_ms, spv_stream_t stream)
+{
+    if (!best || !check_batch(batch)) return SPV_E_ARG;
+    if (reps <= 0) reps = 3;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SPV_E_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return SPV_E_CUDA; }
+    int rc = SPV_SUCCESS, found = 0;
+    float bms = 0.f;
+    spv_config b{};
+    for (const auto &shape : kTileShapes) {
+        spv_config c{};
+        c.tile_words = shape[0];
+        c.threads = shape[1];
+        if (spv_workspace_bytes(batch->n_modules, batch->n_words, 0, &c) > workspace_bytes) continue;
+        rc = spv_process_batch(batch, table, status, err_row, validate, out_words, 1, workspace, workspace_bytes, 0,
+                               &c, stream);                       // warm-up
+        if (rc != SPV_SUCCESS) break;
+        if (cudaEventRecord(e0, st) != cudaSuccess) { rc = SPV_E_CUDA; break; }
+        for (int r = 0; r < reps && rc == SPV_SUCCESS; r++)
+            rc = spv_process_batch(batch, table, status, err_row, validate, out_words, 1, workspace,
+                                   workspace_bytes, 0, &c, stream);
+        if (rc != SPV_SUCCESS) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = SPV_E_CUDA; break; }
+        ms /= (float)reps;
+        if (!found || ms < bms) { found = 1; bms = ms; b = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SPV_SUCCESS) return rc;
+    if (!found) return SPV_E_WORKSPACE;
+    // leave the outputs of the chosen shape behind
+    rc = spv_process_batch(batch, table, status, err_row, validate, out_words, 1, workspace, workspace_bytes, 0, &b,
+                           stream);
+    if (rc != SPV_SUCCESS) return rc;
+    *best = b;
+    if (best_ms) *best_ms = bms;
+    return cudaStreamSynchronize(st) == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;
+}
+
 extern "C" int spv_decode_batch(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row,
                                 void *workspace, size_t workspace_bytes, const spv_config *cfg, spv_stream_t stream)
 {
@@ -1141,7 +1196,9 @@ extern "C" int spv_validate_batch(const spv_batch *batch, const spv_table *table
                                   spv_stream_t stream)
 {
     Cfg c;
-    if (!check_batch(batch) || !table || !status || !err_row || resolve_cfg(nullptr, &c)) return SPV_E_ARG;
+    if (!check_batch(batch) || !table || !status || !err_row ||
+        resolve_cfg(nullptr, &c, batch->n_modules, batch->n_words))
+        return SPV_E_ARG;
     if (!table->op || !table->wc || !table->off || !table->rid || !table->mod || !table->mod_first_row ||
         !table->mod_n_instr)
         return SPV_E_ARG;
@@ -1214,7 +1271,7 @@ extern "C" int spv_process_batch_noalloc(const spv_batch *batch, spv_table *tabl
                                          int recompute_bound, const spv_config *cfg, spv_stream_t stream)
 {
     Cfg c;
-    if (!check_batch(batch) || resolve_cfg(cfg, &c)) return SPV_E_ARG;
+    if (!check_batch(batch) || resolve_cfg(cfg, &c, batch->n_modules, batch->n_words)) return SPV_E_ARG;
     if (c.per_module) return SPV_E_UNSUPPORTED;
     if (make_layout(batch->n_modules, batch->n_words, 0, c.T).total > (size_t)SPV_NOALLOC_SCRATCH_BYTES)
         return SPV_E_WORKSPACE;

@@ -65,7 +65,12 @@ int slot_reserve(Slot &s, int64_t cap_words, int32_t cap_mods, bool encode)
     uint64_t text_cap = std::max<uint64_t>(s.text_cap, 10ull * (uint64_t)cap_words + 4096);
     slot_free_buffers(s);
     const int64_t rows = cap_words;                      // rows never exceed words
-    const size_t ws_bytes = spv_workspace_bytes(cap_mods, cap_words, 0, nullptr);
+    // the default tile shape follows each chunk's mean module size; the
+    // shape with the most tiles (2048 x 128) bounds the workspace of both
+    spv_config small_tiles{};
+    small_tiles.tile_words = 2048;
+    small_tiles.threads = 128;
+    const size_t ws_bytes = spv_workspace_bytes(cap_mods, cap_words, 0, &small_tiles);
     const size_t dws_bytes = spv_dis_workspace_bytes(cap_mods, cap_words, rows, 0);
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = up256(o + bytes); return at; };

@@ -391,7 +391,10 @@ extern "C" spv_server *spv_serve_create(const spv_serve_cfg *cfg)
     s->dev = s->cfg.device;
     if (cudaSetDevice(s->dev) != cudaSuccess) { delete s; return nullptr; }
     int64_t W = s->cfg.max_batch_words;
-    size_t per_batch = spv_workspace_bytes(s->cfg.max_batch_modules, W, 0, nullptr) +
+    spv_config small_tiles{};                      // the default shape with the most tiles bounds the workspace
+    small_tiles.tile_words = 2048;
+    small_tiles.threads = 128;
+    size_t per_batch = spv_workspace_bytes(s->cfg.max_batch_modules, W, 0, &small_tiles) +
                        spv_dis_workspace_bytes(s->cfg.max_batch_modules, W, W, 0) + 12ull * W + 64ull * 4096 +
                        64ull * s->cfg.max_batch_modules + (1 << 20);
     s->dpool_bytes = s->cfg.hbm_cap_bytes + 2 * per_batch + 28ull * W;

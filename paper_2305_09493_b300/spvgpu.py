@@ -90,6 +90,9 @@ def load():
     lib.spv_version.restype = ctypes.c_char_p
     lib.spv_process_batch_noalloc.restype = ctypes.c_int
     lib.spv_process_batch_noalloc.argtypes = [BP, TP, P, P, ctypes.c_int, P, ctypes.c_int, CP, P]
+    lib.spv_autotune_batch.restype = ctypes.c_int
+    lib.spv_autotune_batch.argtypes = [BP, TP, P, P, ctypes.c_int, P, P, sz, ctypes.c_int, CP,
+                                       ctypes.POINTER(ctypes.c_float), P]
     _lib = lib
     return lib
 
@@ -257,6 +260,43 @@ def process(words, mod_off, *, validate=True, encode=False, recompute_bound=True
     _check(rc, "spv_process_batch")
     return {"table": table, "status": status[:m], "err_row": err_row[:m], "out": out if encode else None,
             "workspace": workspace}
+
+
+# the tile shapes the library's autotuner tries
+TILE_SHAPES = ((4096, 256), (8192, 512), (2048, 256), (2048, 128), (1024, 128))
+
+
+def autotune_workspace_bytes(n_modules, n_words, arena_words=0):
+    """Workspace bytes that fit spv_process_batch for every tile shape."""
+    return max(spv_workspace_bytes(n_modules, n_words, arena_words, make_config(t, n)) for t, n in TILE_SHAPES)
+
+
+def autotune(words, mod_off, *, validate=True, encode=True, table=None, workspace=None, out=None, reps=3, stream=None):
+    """spv_autotune_batch: the fastest tile shape of spv_process_batch for
+    this batch. Returns (SpvConfig, mean ms of one call, process outputs of
+    that shape)."""
+    m = mod_off.numel() - 1
+    dev = words.device
+    if table is None:
+        table = Table(m, max(1, words.numel()), dev)
+    if workspace is None:
+        workspace = Workspace.__new__(Workspace)
+        workspace.bytes = autotune_workspace_bytes(m, words.numel())
+        workspace.buf = torch.empty(max(1, workspace.bytes), dtype=torch.uint8, device=dev)
+        workspace.arena_words = 0
+    status = torch.empty(max(1, m), dtype=torch.int32, device=dev)
+    err_row = torch.empty(max(1, m), dtype=torch.int64, device=dev)
+    if encode and out is None:
+        out = torch.empty_like(words)
+    best = SpvConfig()
+    ms = ctypes.c_float(0)
+    rc = load().spv_autotune_batch(ctypes.byref(batch_of(words, mod_off)), ctypes.byref(table.c()), _ptr(status),
+                                   _ptr(err_row), 1 if validate else 0, _ptr(out) if encode else None,
+                                   _ptr(workspace.buf), workspace.bytes, reps, ctypes.byref(best), ctypes.byref(ms),
+                                   _stream(stream))
+    _check(rc, "spv_autotune_batch")
+    return best, ms.value, {"table": table, "status": status[:m], "err_row": err_row[:m],
+                            "out": out if encode else None, "workspace": workspace}
 
 
 def decode(words, mod_off, **kw):

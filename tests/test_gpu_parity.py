@@ -506,3 +506,58 @@ def test_big_tiles_on_generated_batch(gpu):
     n_instr, n_k = synth.batch_shape(80, 23, median=3000, lo=200, hi=40000)
     w, off = synth.batch(n_instr, n_k, 23)
     check(gpu, w, off, cfg=gpu.make_config(tile_words=8192, threads=512))
+
+
+# ---------------------------------------------------------------------------
+# autotuning and CUDA-graph replay
+# ---------------------------------------------------------------------------
+def test_autotune_returns_a_built_shape_with_exact_outputs(gpu):
+    n_instr, n_k = synth.batch_shape(60, 77, median=2000, lo=200, hi=20000)
+    w, off = synth.batch(n_instr, n_k, 77)
+    wd = torch.from_numpy(w.view(np.int32)).cuda()
+    od = torch.from_numpy(off).cuda()
+    cfg, ms, r = gpu.autotune(wd, od, reps=2)
+    assert (cfg.tile_words, cfg.threads) in gpu.TILE_SHAPES and ms > 0
+    d = oracle.decode(w, off)
+    st, er = oracle.validate(w, off)
+    assert_table_equal(r["table"].to_numpy(), d, len(off) - 1)
+    assert np.array_equal(r["status"].cpu().numpy().view(np.uint32), st)
+    assert np.array_equal(r["err_row"].cpu().numpy(), er)
+    assert np.array_equal(r["out"].cpu().numpy().view(np.uint32), oracle.encode(w, off, d, True))
+
+
+def test_step_captured_in_a_cuda_graph_replays_exactly(gpu):
+    """decode + validate + encode + disassemble captured once into a CUDA
+    graph and replayed: every replay reproduces the oracle's outputs (the
+    persistent launches have no host synchronisation inside)."""
+    n_instr, n_k = synth.batch_shape(40, 78, median=1500, lo=200, hi=10000)
+    w, off = synth.batch(n_instr, n_k, 78)
+    m = len(off) - 1
+    wd = torch.from_numpy(w.view(np.int32)).cuda()
+    od = torch.from_numpy(off).cuda()
+    want, woff = oracle.disassemble(w, off, True, True)
+    table = gpu.Table(m, len(w), wd.device)
+    ws = gpu.Workspace(m, len(w), wd.device)
+    dws = gpu.DisWorkspace(m, len(w), len(w), wd.device)
+    out = torch.empty_like(wd)
+    text = torch.empty(len(want) + 16, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):                      # warm up outside the capture
+        gpu.process(wd, od, encode=True, table=table, workspace=ws, out=out, stream=s)
+        gpu.disassemble(wd, od, table, workspace=dws, text=text, sync=False, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        r = gpu.process(wd, od, encode=True, table=table, workspace=ws, out=out)
+        _, toff, dst = gpu.disassemble(wd, od, table, workspace=dws, text=text, sync=False)
+    d = oracle.decode(w, off)
+    st, er = oracle.validate(w, off)
+    for _ in range(3):
+        out.zero_(); text.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(r["status"].cpu().numpy().view(np.uint32), st)
+        assert np.array_equal(r["err_row"].cpu().numpy(), er)
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.encode(w, off, d, True))
+        assert bytes(text[:len(want)].cpu().numpy()) == want
+        assert np.array_equal(toff.cpu().numpy(), woff)
