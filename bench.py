@@ -34,7 +34,7 @@ METRIC = "SPIR-V GB/s decode+validate+disasm, batched vs per-module; serve p50/p
 L2_BYTES = 126 * 2**20
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=20_000.0, help="Poisson arrival rate of the serve leg (modules/s)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="duration of the serve leg (0: skip)")
     ap.add_argument("--e2e-chunk-words", type=int, default=0, help="chunk size of the end-to-end pipeline (0: library default)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload(name, rank, n_mod=10_000):
@@ -76,6 +76,26 @@ def dist_setup(n):
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
     return rank, world
+
+
+def max_over_ranks(values, world):
+    """Each value reduced to its maximum over all ranks (the step time of the
+    slowest rank). The tensor lives where the process group's backend wants
+    it: host memory under gloo, the current GPU under NCCL."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cpu") if dist.get_backend() == "gloo" else torch.device("cuda", torch.cuda.current_device())
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu().tolist()]
+
+
+def job_gbs(world, words_per_rank, ms):
+    """Whole-job input throughput: every rank processes its own batch of
+    words_per_rank words in (at most) ms milliseconds."""
+    return world * 4 * words_per_rank / (ms * 1e-3) / 1e9
 
 
 def measured_peaks():
@@ -405,12 +425,9 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     t_ms = float(np.sum(step_ms))
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks([t_ms], world)[0]
     ms_per_step = t_ms / args.steps
-    value = world * 4 * W / (ms_per_step * 1e-3) / 1e9
+    value = job_gbs(world, W, ms_per_step)
 
     # roofline of the dominant kernel
     launches = sum(v[0] for v in prof.values())
@@ -483,15 +500,12 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     serial_ms = e0.elapsed_time(e1) / ksteps
-    if world > 1:
-        tt = torch.tensor([e2e_ms, serial_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms, serial_ms = float(tt[0].item()), float(tt[1].item())
-    e2e = {"value": world * 4 * W / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+    e2e_ms, serial_ms = max_over_ranks([e2e_ms, serial_ms], world)
+    e2e = {"value": job_gbs(world, W, e2e_ms), "unit": "GB/s",
            "h2d_bytes_per_step": 4 * W + 8 * (M + n_chunks),
            "d2h_bytes_per_step": 4 * M + 8 * M + 8 * (M + n_chunks) + Ltext,
            "ms_per_step": e2e_ms, "api": "spv_pipe_run", "chunks": n_chunks, "results_exact": e2e_ok,
-           "serial_one_stream": {"ms_per_step": serial_ms, "value": world * 4 * W / (serial_ms * 1e-3) / 1e9}}
+           "serial_one_stream": {"ms_per_step": serial_ms, "value": job_gbs(world, W, serial_ms)}}
 
     # batched vs per-module launches (decode+validate+encode, same exact output)
     cmp = None
