@@ -67,6 +67,10 @@ def _L():
         lib.orc_num_ops.restype = ctypes.c_int
         lib.orc_op_at.restype = ctypes.c_uint32
         lib.orc_op_at.argtypes = [ctypes.c_int]
+        lib.orc_layout.restype = None
+        lib.orc_layout.argtypes = [P, P, P, ctypes.c_int32, P, P]
+        lib.orc_layout_class.restype = ctypes.c_int
+        lib.orc_layout_class.argtypes = [ctypes.c_uint32, P]
         _lib = lib
     return _lib
 
@@ -101,6 +105,29 @@ def decode(words, mod_off) -> dict:
         t[k] = t[k][:n]
     t["n_rows"] = int(n)
     return t
+
+
+LAYOUT_STATUS = ["OK", "SECTION_ORDER", "OUTSIDE_FUNCTION", "IN_FUNCTION", "BLOCK", "UNCLOSED"]
+
+
+def layout(words, mod_off):
+    """Logical layout and scopes of every module's decoded rows (see
+    orc_layout); returns (status[M] uint32, err_row[M] int64)."""
+    words, mod_off = _prep(words, mod_off)
+    d = decode(words, mod_off)
+    m = len(mod_off) - 1
+    status = np.zeros(m, np.uint32)
+    err_row = np.zeros(m, np.int64)
+    op = d["op"] if len(d["op"]) else np.zeros(1, np.uint16)
+    _L().orc_layout(_p(np.ascontiguousarray(op)), _p(d["first_row"]), _p(d["n_instr"]), m, _p(status), _p(err_row))
+    return status, err_row
+
+
+def layout_class(op: int):
+    """(class, section) of an opcode for the layout check (see orc_layout_class)."""
+    sec = ctypes.c_int()
+    c = _L().orc_layout_class(op, ctypes.byref(sec))
+    return int(c), int(sec.value)
 
 
 def validate(words, mod_off):

@@ -676,6 +676,125 @@ void orc_validate(const uint32_t *words, const int64_t *mod_off, int32_t n_mod,
 }
 
 /* ------------------------------------------------------------------ */
+/* logical layout and scopes                                            */
+/* ------------------------------------------------------------------ */
+/*
+ * Section 3.4.1, "Handling Different Scopes within a SPIR-V Module": the
+ * module scope holds the global declarations (capabilities, memory model,
+ * entry points, debug names, decorations, types, constants, global
+ * variables) and the functions; a function holds its parameters and its
+ * body; a body is a sequence of basic blocks, each opened by a label.  The
+ * paper gives the scopes, not the checks; the reading used here:
+ *   - module-scope instructions come in the SPIR-V specification's section
+ *     order: capabilities (1), extensions (2), extended-instruction imports
+ *     (3), memory model (4), entry points (5), execution modes (6), debug
+ *     instructions (7), decorations (8), types / constants / global
+ *     variables (9), functions (10); a row of a lower section after one of a
+ *     higher section is SECTION_ORDER;
+ *   - OpFunction opens a function (only at module scope), its parameters
+ *     follow directly, then either OpFunctionEnd (a declaration) or blocks;
+ *     a block opens with OpLabel and closes with a terminator (OpBranch,
+ *     OpBranchConditional, OpReturn, OpReturnValue, OpUnreachable); after a
+ *     terminator comes OpLabel or OpFunctionEnd;
+ *   - OpVariable and OpUndef are global declarations at module scope and
+ *     body instructions inside a function; OpNop and opcodes outside the
+ *     table are allowed anywhere;
+ *   - errors: OUTSIDE_FUNCTION (a function-scope instruction at module
+ *     scope), IN_FUNCTION (a module-scope instruction, or a second
+ *     OpFunction, inside a function), BLOCK (a body instruction or
+ *     terminator before the first label or after a terminator, a label in
+ *     an open block, a parameter after a label, OpFunctionEnd in an open
+ *     block), UNCLOSED (the rows end inside a function; its row is the
+ *     module's row count).  The first error in row order is the module's.
+ */
+enum { LC_ANY, LC_SEC, LC_MIXED, LC_FUNCTION, LC_PARAM, LC_FUNCEND, LC_LABEL, LC_TERM, LC_BODY };
+enum { LS_OK, LS_SECTION_ORDER, LS_OUTSIDE_FUNCTION, LS_IN_FUNCTION, LS_BLOCK, LS_UNCLOSED };
+
+int orc_layout_class(uint32_t op, int *section)
+{
+    *section = 0;
+    switch (op) {
+    case 0: return LC_ANY;                                     /* OpNop */
+    case 17: *section = 1; return LC_SEC;                      /* OpCapability */
+    case 10: *section = 2; return LC_SEC;                      /* OpExtension */
+    case 11: *section = 3; return LC_SEC;                      /* OpExtInstImport */
+    case 14: *section = 4; return LC_SEC;                      /* OpMemoryModel */
+    case 15: *section = 5; return LC_SEC;                      /* OpEntryPoint */
+    case 16: *section = 6; return LC_SEC;                      /* OpExecutionMode */
+    case 3: case 5: case 6: case 7: *section = 7; return LC_SEC;  /* OpSource OpName OpMemberName OpString */
+    case 71: *section = 8; return LC_SEC;                      /* OpDecorate */
+    case 1: case 59: *section = 9; return LC_MIXED;            /* OpUndef, OpVariable */
+    case 54: *section = 10; return LC_FUNCTION;                /* OpFunction */
+    case 55: return LC_PARAM;                                  /* OpFunctionParameter */
+    case 56: return LC_FUNCEND;                                /* OpFunctionEnd */
+    case 248: return LC_LABEL;                                 /* OpLabel */
+    case 249: case 250: case 253: case 254: case 255: return LC_TERM;
+    default: break;
+    }
+    if (!find_op(op)) return LC_ANY;
+    if (op >= 19 && op <= 46) { *section = 9; return LC_SEC; }   /* OpType* and OpConstant* */
+    return LC_BODY;
+}
+
+/* Per module (rows first_row[m] .. first_row[m] + n_instr[m] - 1 of a decode):
+ * layout status and the module-local row it refers to (-1 when LS_OK). */
+void orc_layout(const uint16_t *op, const int64_t *first_row, const uint32_t *n_instr, int32_t n_mod,
+                uint32_t *status, int64_t *err_row)
+{
+    enum { MODULE, HEAD, BLOCK, AFTER };
+    for (int32_t m = 0; m < n_mod; m++) {
+        int st = MODULE, maxsec = 0;
+        uint32_t e = LS_OK;
+        int64_t row = -1;
+        for (uint32_t i = 0; i < n_instr[m] && e == LS_OK; i++) {
+            int sec;
+            int c = orc_layout_class(op[first_row[m] + i], &sec);
+            switch (c) {
+            case LC_ANY:
+                break;
+            case LC_SEC:
+            case LC_MIXED:
+            case LC_FUNCTION:
+                if (st == MODULE) {
+                    if (sec < maxsec) e = LS_SECTION_ORDER;
+                    else maxsec = sec;
+                    if (c == LC_FUNCTION && e == LS_OK) st = HEAD;
+                } else if (c == LC_MIXED && st == BLOCK) {
+                    /* a variable or undef inside a block */
+                } else if (c == LC_MIXED) {
+                    e = LS_BLOCK;
+                } else {
+                    e = LS_IN_FUNCTION;
+                }
+                break;
+            case LC_PARAM:
+                if (st != HEAD) e = st == MODULE ? LS_OUTSIDE_FUNCTION : LS_BLOCK;
+                break;
+            case LC_LABEL:
+                if (st == HEAD || st == AFTER) st = BLOCK;
+                else e = st == MODULE ? LS_OUTSIDE_FUNCTION : LS_BLOCK;
+                break;
+            case LC_BODY:
+                if (st != BLOCK) e = st == MODULE ? LS_OUTSIDE_FUNCTION : LS_BLOCK;
+                break;
+            case LC_TERM:
+                if (st == BLOCK) st = AFTER;
+                else e = st == MODULE ? LS_OUTSIDE_FUNCTION : LS_BLOCK;
+                break;
+            case LC_FUNCEND:
+                if (st == HEAD || st == AFTER) st = MODULE;
+                else e = st == MODULE ? LS_OUTSIDE_FUNCTION : LS_BLOCK;
+                break;
+            }
+            if (e != LS_OK) row = i;
+        }
+        if (e == LS_OK && st != MODULE) { e = LS_UNCLOSED; row = n_instr[m]; }
+        status[m] = e;
+        err_row[m] = row;
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Encode.                                                             */
 /* ------------------------------------------------------------------ */
 
