@@ -507,6 +507,24 @@ def main():
            "ms_per_step": e2e_ms, "api": "spv_pipe_run", "chunks": n_chunks, "results_exact": e2e_ok,
            "serial_one_stream": {"ms_per_step": serial_ms, "value": job_gbs(world, W, serial_ms)}}
 
+    # logical layout and scopes over the decoded table (spv_layout_batch):
+    # reads the op column (2 bytes per row) and the module row offsets
+    lay_ms = []
+    for k in range(6):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if flush is not None:
+            flush.zero_()
+        a.record(stream)
+        lst, _ = spvgpu.layout(table, M)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k:
+            lay_ms.append(a.elapsed_time(b))
+    lay = float(np.median(lay_ms))
+    layout_leg = {"scope": "section order and function / block nesting over the decoded table",
+                  "ms": lay, "rows_per_s": N / (lay * 1e-3), "achieved_gbs": (2 * N + 8 * M) / (lay * 1e-3) / 1e9,
+                  "all_clean": bool((lst == 0).all().item())}
+
     # batched vs per-module launches (decode+validate+encode, same exact output)
     cmp = None
     if not args.no_per_module and world == 1:
@@ -557,6 +575,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched_vs_per_module": cmp,
+        "layout": layout_leg,
         "serve": serve,
         "clocks": clk,
         "gpu_launches": launches,

@@ -193,6 +193,44 @@ int spv_autotune_batch(const spv_batch *batch, spv_table *table, uint32_t *statu
                        uint32_t *out_words, void *workspace, size_t workspace_bytes, int reps, spv_config *best,
                        float *best_ms, spv_stream_t stream);
 
+/*
+ * spv_layout_batch -- logical layout and scopes of every module's decoded
+ * rows (section 3.4.1: module, function and block scopes; the checks follow
+ * the SPIR-V logical layout the paper builds on). Module-scope rows must
+ * come in section order: capabilities (1), extensions (2), extended-
+ * instruction imports (3), memory model (4), entry points (5), execution
+ * modes (6), debug instructions (7), decorations (8), types, constants and
+ * global variables (9), functions (10). OpFunction opens a function at
+ * module scope; its parameters follow; then OpFunctionEnd (a declaration)
+ * or blocks, each opened by OpLabel and closed by a terminator (OpBranch,
+ * OpBranchConditional, OpReturn, OpReturnValue, OpUnreachable), the last
+ * followed by OpFunctionEnd. OpVariable and OpUndef are global declarations
+ * at module scope and body instructions in a block; OpNop and opcodes
+ * outside the table are allowed anywhere. Reads table->op and
+ * table->mod_first_row of a decode (rows of module m: mod_first_row[m] ..
+ * mod_first_row[m + 1] - 1, capped at capacity_rows). Writes
+ * layout_status[n_modules] (spv_layout_status) and layout_err_row: the
+ * module-local row of the first error in row order (the row count for
+ * SPV_LAYOUT_UNCLOSED), -1 when OK. No workspace; asynchronous on stream.
+ */
+enum spv_layout_status {
+    SPV_LAYOUT_OK = 0,
+    SPV_LAYOUT_SECTION_ORDER = 1,      /* a module-scope row of a lower section after one of a higher section */
+    SPV_LAYOUT_OUTSIDE_FUNCTION = 2,   /* a parameter, label, body instruction, terminator or OpFunctionEnd at module scope */
+    SPV_LAYOUT_IN_FUNCTION = 3,        /* a module-scope instruction, or a second OpFunction, inside a function */
+    SPV_LAYOUT_BLOCK = 4,              /* body or terminator before the first label or after a terminator; a label in an
+                                          open block; a parameter after a label; OpFunctionEnd in an open block */
+    SPV_LAYOUT_UNCLOSED = 5            /* the rows end inside a function */
+};
+int spv_layout_batch(const spv_table *table, int32_t n_modules, uint32_t *layout_status, int64_t *layout_err_row,
+                     spv_stream_t stream);
+/* Layout class of an opcode in the library's table (host query):
+ * 0 neutral, 1 module section, 2 OpUndef / OpVariable (section 9 at module
+ * scope, body in a block), 3 OpFunction (section 10), 4 OpFunctionParameter,
+ * 5 OpFunctionEnd, 6 OpLabel, 7 terminator, 8 body; *section is the module
+ * section (0 when none). Returns 0. */
+int spv_op_layout(uint32_t opcode, int *layout_class, int *section);
+
 /* spv_decode_batch -- spv_process_batch with validate = 0 and no encode. */
 int spv_decode_batch(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row,
                      void *workspace, size_t workspace_bytes, const spv_config *cfg, spv_stream_t stream);

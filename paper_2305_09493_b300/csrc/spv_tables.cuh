@@ -318,6 +318,7 @@ struct Tables {
     uint8_t vunknown[NUM_VKINDS];   // operand code used for the parameters of an unknown value (A_END: none)
     uint64_t cap_dep[64];           // bit b set in cap_dep[a]: declaring a declares b
     uint8_t shape[256];             // text shape class: opcodes with the same operand list share one (1 = unknown)
+    uint8_t layout[256];            // layout class (low 4 bits, spv_layout_class) and module section (high 4 bits)
     char names[NAME_POOL];
     int name_used;
 };
@@ -346,6 +347,34 @@ constexpr void fill_enum(Tables &t, EnDesc *dst, const EnSrc (&src)[N], bool bit
         d.name_lo = (uint8_t)(off & 0xff);
     }
 }
+
+// Layout classes of the opcodes that are not plain body instructions
+// (section 3.4.1 scopes; sections in the SPIR-V specification's module
+// order): {opcode, class, section}. Every other opcode of the table is a
+// body instruction; opcodes outside the table are neutral.
+struct LayoutSrc { uint16_t op; uint8_t cls, sec; };
+enum : uint8_t { LCL_ANY = 0, LCL_SECTION = 1, LCL_MIXED = 2, LCL_FUNCTION = 3, LCL_PARAM = 4, LCL_FUNCEND = 5,
+                 LCL_LABEL = 6, LCL_TERM = 7, LCL_BODY = 8 };
+constexpr LayoutSrc LAYOUT_LIST[] = {
+    {0, LCL_ANY, 0},                                                        // OpNop
+    {17, LCL_SECTION, 1},                                                   // capabilities
+    {10, LCL_SECTION, 2},                                                   // extensions
+    {11, LCL_SECTION, 3},                                                   // extended-instruction imports
+    {14, LCL_SECTION, 4},                                                   // memory model
+    {15, LCL_SECTION, 5},                                                   // entry points
+    {16, LCL_SECTION, 6},                                                   // execution modes
+    {3, LCL_SECTION, 7}, {5, LCL_SECTION, 7}, {6, LCL_SECTION, 7}, {7, LCL_SECTION, 7},   // debug
+    {71, LCL_SECTION, 8},                                                   // decorations
+    {19, LCL_SECTION, 9}, {20, LCL_SECTION, 9}, {21, LCL_SECTION, 9}, {22, LCL_SECTION, 9},
+    {23, LCL_SECTION, 9}, {28, LCL_SECTION, 9}, {30, LCL_SECTION, 9}, {32, LCL_SECTION, 9},
+    {33, LCL_SECTION, 9},                                                   // types
+    {41, LCL_SECTION, 9}, {42, LCL_SECTION, 9}, {43, LCL_SECTION, 9}, {44, LCL_SECTION, 9},
+    {46, LCL_SECTION, 9},                                                   // constants
+    {1, LCL_MIXED, 9}, {59, LCL_MIXED, 9},                                  // OpUndef, OpVariable
+    {54, LCL_FUNCTION, 10}, {55, LCL_PARAM, 0}, {56, LCL_FUNCEND, 0},
+    {248, LCL_LABEL, 0},
+    {249, LCL_TERM, 0}, {250, LCL_TERM, 0}, {253, LCL_TERM, 0}, {254, LCL_TERM, 0}, {255, LCL_TERM, 0},
+};
 
 constexpr Tables build_tables()
 {
@@ -379,6 +408,7 @@ constexpr Tables build_tables()
             d.id_mask = fast ? mask : 0;
             d.nfixed = fast ? (uint8_t)nfixed : 0;
         }
+        t.layout[o.op] = LCL_BODY;
         int len = cstrlen(o.name);
         d.name_off = (uint16_t)t.name_used;
         d.name_len = (uint8_t)len;
@@ -419,6 +449,7 @@ constexpr Tables build_tables()
         }
         t.shape[o] = (uint8_t)(found >= 0 ? found : next_shape++);
     }
+    for (const LayoutSrc &l : LAYOUT_LIST) t.layout[l.op] = (uint8_t)(l.cls | (l.sec << 4));
     return t;
 }
 

@@ -90,6 +90,10 @@ def load():
     lib.spv_version.restype = ctypes.c_char_p
     lib.spv_process_batch_noalloc.restype = ctypes.c_int
     lib.spv_process_batch_noalloc.argtypes = [BP, TP, P, P, ctypes.c_int, P, ctypes.c_int, CP, P]
+    lib.spv_layout_batch.restype = ctypes.c_int
+    lib.spv_layout_batch.argtypes = [TP, i32, P, P, P]
+    lib.spv_op_layout.restype = ctypes.c_int
+    lib.spv_op_layout.argtypes = [ctypes.c_uint32, P, P]
     lib.spv_autotune_batch.restype = ctypes.c_int
     lib.spv_autotune_batch.argtypes = [BP, TP, P, P, ctypes.c_int, P, P, sz, ctypes.c_int, CP,
                                        ctypes.POINTER(ctypes.c_float), P]
@@ -297,6 +301,27 @@ def autotune(words, mod_off, *, validate=True, encode=True, table=None, workspac
     _check(rc, "spv_autotune_batch")
     return best, ms.value, {"table": table, "status": status[:m], "err_row": err_row[:m],
                             "out": out if encode else None, "workspace": workspace}
+
+
+LAYOUT_STATUS = ["OK", "SECTION_ORDER", "OUTSIDE_FUNCTION", "IN_FUNCTION", "BLOCK", "UNCLOSED"]
+
+
+def layout(table, n_modules, *, stream=None):
+    """spv_layout_batch over a decoded table: (layout_status[M] int32,
+    layout_err_row[M] int64) device tensors."""
+    dev = table.op.device
+    status = torch.empty(max(1, n_modules), dtype=torch.int32, device=dev)
+    err_row = torch.empty(max(1, n_modules), dtype=torch.int64, device=dev)
+    rc = load().spv_layout_batch(ctypes.byref(table.c()), n_modules, _ptr(status), _ptr(err_row), _stream(stream))
+    _check(rc, "spv_layout_batch")
+    return status[:n_modules], err_row[:n_modules]
+
+
+def op_layout(op):
+    """(layout class, module section) of an opcode in the library's table."""
+    c, sec = ctypes.c_int(), ctypes.c_int()
+    load().spv_op_layout(op, ctypes.byref(c), ctypes.byref(sec))
+    return c.value, sec.value
 
 
 def decode(words, mod_off, **kw):

@@ -75,3 +75,9 @@ def test_bit_enum_tables_agree(kind):
     from paper_2305_09493_b300 import spvgpu
     for b in range(32):
         assert oracle.enum_name(kind, 1 << b) == spvgpu.spv_enum_info(kind, 1 << b), (kind, b)
+
+
+def test_layout_classes_agree():
+    from paper_2305_09493_b300 import spvgpu
+    for op in range(0, 300):
+        assert oracle.layout_class(op) == spvgpu.op_layout(op), op
