@@ -166,14 +166,53 @@ def disassemble(words, mod_off, inline_names: bool = True, header: bool = True):
     return buf.raw[:n], text_off
 
 
+def assemble_one(text: bytes):
+    """Assemble one module's text. Returns (words, 0) or (None, line): the
+    1-based number of the first line that does not parse."""
+    text = bytes(text)
+    cap = len(text) + 64
+    while True:
+        out = np.zeros(cap, np.uint32)
+        n = _L().orc_assemble(text, len(text), _p(out), cap)
+        if n < 0:
+            return None, int(-n)
+        if n <= cap:
+            return out[:n].copy(), 0
+        cap = int(n)
+
+
 def assemble(text: bytes) -> np.ndarray:
     """Assemble one module from text (inverse of disassemble with header)."""
-    cap = len(text) + 64
-    out = np.zeros(cap, np.uint32)
-    n = _L().orc_assemble(text, len(text), _p(out), cap)
-    if n < 0:
-        raise ValueError(f"assemble: parse error at line {-n}")
-    return out[:n].copy()
+    words, line = assemble_one(text)
+    if words is None:
+        raise ValueError(f"assemble: parse error at line {line}")
+    return words
+
+
+# Assembler module status codes.
+ASM_STATUS = ["OK", "SYNTAX"]
+
+
+def assemble_batch(text: bytes, text_off):
+    """Assemble every module of a batch: module m's text is
+    text[text_off[m]:text_off[m+1]]. Returns (words, word_off, status,
+    err_line): a module that does not parse gets no words, status SYNTAX and
+    the number of its first bad line (-1 when OK)."""
+    text = bytes(text)
+    text_off = np.asarray(text_off, np.int64)
+    n = len(text_off) - 1
+    parts, word_off = [], np.zeros(n + 1, np.int64)
+    status = np.zeros(n, np.uint32)
+    err = np.full(n, -1, np.int64)
+    for m in range(n):
+        w, line = assemble_one(text[text_off[m]:text_off[m + 1]])
+        if w is None:
+            status[m], err[m] = 1, line
+            w = np.zeros(0, np.uint32)
+        parts.append(w)
+        word_off[m + 1] = word_off[m] + len(w)
+    words = np.concatenate(parts) if parts else np.zeros(0, np.uint32)
+    return words.astype(np.uint32), word_off, status, err
 
 
 def op_info(op: int):

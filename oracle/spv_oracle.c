@@ -1,7 +1,7 @@
 /*
  * spv_oracle.c -- the plain, sequential CPU definition of the batched SPIR-V
- * hot path: decode, validate, encode, disassemble (and assemble, used to pin
- * the disassembler by round trip).
+ * hot path: decode, validate, encode, disassemble, the logical-layout check,
+ * and assemble (text back to words).
  *
  * TEST INFRASTRUCTURE. Only tests/, __graft_entry__.smoke() and bench.py's
  * CPU-baseline / reference arm may load or call this library. The CUDA
@@ -30,6 +30,8 @@
  *               bound recomputation of section 3.4.1.
  *   disassemble section 3.4.4 and Listing 10 (options "inline names" and
  *               "header"); one line per instruction as in Listing 8.
+ *   assemble    section 3.4.4 "Dis/Assembler": the inverse of the text form,
+ *               with a hash table from id names to ids.
  *
  * Every decision the paper leaves open is listed, with its reading, in the
  * repository's design notes; the short form is repeated at each function.
@@ -1057,10 +1059,39 @@ int64_t orc_disassemble(const uint32_t *words, const int64_t *mod_off, int32_t n
 }
 
 /* ------------------------------------------------------------------ */
-/* Assemble (text -> one module). Inverse of the disassembler for      */
-/* modules it prints with header lines.                                */
+/* Assemble (text -> one module), section 3.4.4 "Dis/Assembler": the   */
+/* text form the disassembler prints, read back into words, with the   */
+/* map from id names to ids that the paper's assembler keeps in a hash */
+/* table.                                                              */
+/*                                                                     */
+/* The text form, line by line ('\n' ends a line; a final '\n' does    */
+/* not start another; lines are numbered from 1):                      */
+/*  - an empty line is skipped;                                        */
+/*  - a line starting with ';' is a comment; exactly                   */
+/*    "; Version: A.B" (A, B <= 255), "; Generator: 0xH",              */
+/*    "; Bound: N" and "; Schema: N" (values < 2^32, nothing after     */
+/*    them) set the header words; the last such line wins;             */
+/*  - any other line is one instruction: tokens split by spaces; a     */
+/*    token that starts with '"' runs to the next '"' not escaped by   */
+/*    '\' (an unclosed one is an error);                               */
+/*    "[%r =] OpName operands" or "Op<decimal> 0xHHHHHHHH..." (raw).   */
+/* Ids: "%<digits>" and "%<name>_<digits>" are the id <digits>         */
+/* (< 2^32); any other "%<name>" is a named id: the distinct names get */
+/* ids M+1, M+2, ... in order of first appearance in the module text,  */
+/* M the largest explicit id of the module (0 if none).                */
+/* Literals: decimal, < 2^32. Strings: "\xHH" is byte HH, '\' before   */
+/* any other byte is that byte. OpConstant's value: two or more tokens */
+/* are one word each; one token is a decimal integer (< 2^64) or a     */
+/* float literal ([+-] then inf, nan, C99 hex or decimal), as wide as  */
+/* the result type: the first OpTypeInt / OpTypeFloat of the module    */
+/* that defines that id (a 32-bit integer if none). A float literal of */
+/* a 32-bit type is rounded to double, then to float, both to nearest  */
+/* even. Enumerants: the name, or decimal; bit enums also "None" and   */
+/* "A|B". An instruction has at most 65535 words.                      */
+/* Header: magic, version (default 1.2), generator (0), bound (the     */
+/* Bound line, else the largest id + 1), schema (0).                   */
 /* ------------------------------------------------------------------ */
-typedef struct { const char *s; size_t n; } Span;
+typedef struct { const char *s; size_t n; int open; } Span;
 
 static int is_raw_word(Span t)
 {
@@ -1069,29 +1100,71 @@ static int is_raw_word(Span t)
     return 1;
 }
 
-static int parse_id(Span t, uint32_t *id)
+/* decimal digits only, at least one, value <= max */
+static int parse_dec(const char *s, size_t n, uint64_t max, uint64_t *v)
+{
+    if (n == 0) return -1;
+    uint64_t a = 0;
+    for (size_t i = 0; i < n; i++) {
+        if (!isdigit((unsigned char)s[i])) return -1;
+        uint64_t d = (uint64_t)(s[i] - '0');
+        if (a > (max - d) / 10) return -1;
+        a = a * 10 + d;
+    }
+    *v = a;
+    return 0;
+}
+
+static int parse_u32(Span t, uint32_t *v)
+{
+    uint64_t u;
+    if (parse_dec(t.s, t.n, 0xffffffffull, &u)) return -1;
+    *v = (uint32_t)u;
+    return 0;
+}
+
+/* Id token: 0 explicit (*id set), 1 named, -1 not an id. */
+static int classify_id(Span t, uint32_t *id)
 {
     if (t.n < 2 || t.s[0] != '%') return -1;
-    size_t i = t.n;
-    while (i > 1 && isdigit((unsigned char)t.s[i - 1])) i--;
-    if (i == t.n) return -1;
-    if (i != 1 && t.s[i - 1] != '_') return -1;
-    *id = (uint32_t)strtoull(t.s + i, NULL, 10);
+    size_t j = t.n;
+    while (j > 1 && isdigit((unsigned char)t.s[j - 1])) j--;
+    if (j == t.n || (j != 1 && t.s[j - 1] != '_')) return 1;
+    uint64_t u;
+    if (parse_dec(t.s + j, t.n - j, 0xffffffffull, &u)) return -1;
+    *id = (uint32_t)u;
     return 0;
 }
 
-static int parse_u64(Span t, uint64_t *v)
+/* Float literal: the whole token must match
+ *   [+-]? ( inf | nan | 0[xX] H* [. H*] [[pP] [+-]? D+] | D* [. D*] [[eE] [+-]? D+] )
+ * with at least one digit in the mantissa. */
+static int is_float_literal(Span t)
 {
-    if (t.n == 0) return -1;
-    for (size_t i = 0; i < t.n; i++) if (!isdigit((unsigned char)t.s[i])) return -1;
-    char b[32]; if (t.n >= sizeof b) return -1;
-    memcpy(b, t.s, t.n); b[t.n] = 0;
-    *v = strtoull(b, NULL, 10);
-    return 0;
+    size_t i = 0, n = t.n;
+    const char *s = t.s;
+    if (i < n && (s[i] == '+' || s[i] == '-')) i++;
+    if (n - i == 3 && (strncmp(s + i, "inf", 3) == 0 || strncmp(s + i, "nan", 3) == 0)) return 1;
+    int hex = (n - i >= 2 && s[i] == '0' && (s[i + 1] == 'x' || s[i + 1] == 'X'));
+    if (hex) i += 2;
+    size_t digits = 0;
+    while (i < n && (hex ? isxdigit((unsigned char)s[i]) : isdigit((unsigned char)s[i]))) { i++; digits++; }
+    if (i < n && s[i] == '.') {
+        i++;
+        while (i < n && (hex ? isxdigit((unsigned char)s[i]) : isdigit((unsigned char)s[i]))) { i++; digits++; }
+    }
+    if (digits == 0) return 0;
+    if (i < n && (hex ? (s[i] == 'p' || s[i] == 'P') : (s[i] == 'e' || s[i] == 'E'))) {
+        i++;
+        if (i < n && (s[i] == '+' || s[i] == '-')) i++;
+        size_t e = 0;
+        while (i < n && isdigit((unsigned char)s[i])) { i++; e++; }
+        if (e == 0) return 0;
+    }
+    return i == n;
 }
 
-/* Tokeniser: splits on spaces, keeps quoted strings (with escapes) whole. */
-static int tokenize(const char *s, size_t n, Span *toks, int maxt)
+static int tokenize(const char *s, size_t n, Span *toks)
 {
     int k = 0;
     size_t i = 0;
@@ -1099,15 +1172,16 @@ static int tokenize(const char *s, size_t n, Span *toks, int maxt)
         while (i < n && s[i] == ' ') i++;
         if (i >= n) break;
         size_t b = i;
+        int open = 0;
         if (s[i] == '"') {
             i++;
-            while (i < n && s[i] != '"') { if (s[i] == '\\') i++; i++; }
-            i++;
+            while (i < n && s[i] != '"') i += (s[i] == '\\') ? 2 : 1;
+            if (i >= n) { open = 1; i = n; }
+            else i++;
         } else {
             while (i < n && s[i] != ' ') i++;
         }
-        if (k >= maxt) return -1;
-        toks[k].s = s + b; toks[k].n = (i > n ? n : i) - b; k++;
+        toks[k].s = s + b; toks[k].n = i - b; toks[k].open = open; k++;
     }
     return k;
 }
@@ -1115,30 +1189,119 @@ static int tokenize(const char *s, size_t n, Span *toks, int maxt)
 typedef struct { uint32_t *out; int64_t n, cap; } Words;
 static void put_word(Words *W, uint32_t v) { if (W->n < W->cap) W->out[W->n] = v; W->n++; }
 
+static int hexval(int c)
+{
+    if (c >= '0' && c <= '9') return c - '0';
+    if (c >= 'a' && c <= 'f') return c - 'a' + 10;
+    if (c >= 'A' && c <= 'F') return c - 'A' + 10;
+    return -1;
+}
+
 static int put_string_tok(Words *W, Span t)
 {
-    if (t.n < 2 || t.s[0] != '"' || t.s[t.n - 1] != '"') return -1;
-    uint8_t bytes[65536 * 4]; size_t nb = 0;
-    for (size_t i = 1; i + 1 < t.n; i++) {
-        unsigned ch = (unsigned char)t.s[i];
+    if (t.n < 2 || t.s[0] != '"' || t.open) return -1;
+    const char *b = t.s + 1;
+    size_t n = t.n - 2, i = 0;
+    uint32_t acc = 0;
+    int k = 0;
+    while (i < n) {
+        unsigned ch = (unsigned char)b[i];
         if (ch == '\\') {
+            if (i + 3 < n && b[i + 1] == 'x' && hexval(b[i + 2]) >= 0 && hexval(b[i + 3]) >= 0) {
+                ch = (unsigned)(hexval(b[i + 2]) * 16 + hexval(b[i + 3]));
+                i += 4;
+            } else {
+                if (i + 1 >= n) return -1;
+                ch = (unsigned char)b[i + 1];
+                i += 2;
+            }
+        } else {
             i++;
-            if (t.s[i] == 'x') { char h[3] = {t.s[i + 1], t.s[i + 2], 0}; ch = (unsigned)strtoul(h, NULL, 16); i += 2; }
-            else ch = (unsigned char)t.s[i];
         }
-        if (nb < sizeof bytes - 4) bytes[nb++] = (uint8_t)ch;
+        acc |= (uint32_t)ch << (8 * k);
+        if (++k == 4) { put_word(W, acc); acc = 0; k = 0; }
     }
-    bytes[nb++] = 0;
-    while (nb % 4) bytes[nb++] = 0;
-    for (size_t i = 0; i < nb; i += 4)
-        put_word(W, (uint32_t)bytes[i] | ((uint32_t)bytes[i + 1] << 8) | ((uint32_t)bytes[i + 2] << 16) | ((uint32_t)bytes[i + 3] << 24));
+    put_word(W, acc);            /* the NUL and the zero padding */
+    return 0;
+}
+
+/* Named ids: an open-addressing hash map from name bytes to the index of
+ * the name's first appearance. */
+typedef struct { const char *s; size_t n; } Name;
+typedef struct { Name *names; int n, cap; int *slot; int nslot; } NameMap;
+
+static uint32_t name_hash(const char *s, size_t n)
+{
+    uint32_t h = 2166136261u;
+    for (size_t i = 0; i < n; i++) { h ^= (unsigned char)s[i]; h *= 16777619u; }
+    return h;
+}
+
+static int namemap_get(NameMap *M, Span t, int insert)
+{
+    if (M->nslot == 0 || (insert && 2 * (M->n + 1) > M->nslot)) {
+        int ns = M->nslot ? 2 * M->nslot : 64;
+        int *sl = (int *)malloc(sizeof(int) * ns);
+        for (int i = 0; i < ns; i++) sl[i] = -1;
+        for (int k = 0; k < M->n; k++) {
+            uint32_t h = name_hash(M->names[k].s, M->names[k].n) % (uint32_t)ns;
+            while (sl[h] >= 0) h = (h + 1) % (uint32_t)ns;
+            sl[h] = k;
+        }
+        free(M->slot); M->slot = sl; M->nslot = ns;
+    }
+    uint32_t h = name_hash(t.s, t.n) % (uint32_t)M->nslot;
+    while (M->slot[h] >= 0) {
+        Name *q = &M->names[M->slot[h]];
+        if (q->n == t.n && memcmp(q->s, t.s, t.n) == 0) return M->slot[h];
+        h = (h + 1) % (uint32_t)M->nslot;
+    }
+    if (!insert) return -1;
+    if (M->n == M->cap) {
+        M->cap = M->cap ? 2 * M->cap : 64;
+        M->names = (Name *)realloc(M->names, sizeof(Name) * M->cap);
+    }
+    M->names[M->n].s = t.s; M->names[M->n].n = t.n;
+    M->slot[h] = M->n;
+    return M->n++;
+}
+
+/* The first OpTypeInt / OpTypeFloat that defines each type id. */
+typedef struct { uint32_t id; uint8_t is_float, width; } TypeDecl;
+
+typedef struct {
+    int pass;                    /* 0: named ids, largest explicit id; 1: type declarations; 2: words */
+    Span *tk; int nt, ti;
+    Words *W;
+    NameMap names;
+    uint64_t max_explicit;
+    TypeDecl *types; int ntypes, captypes;
+    uint32_t rtype;              /* result type of the instruction being assembled */
+    uint64_t max_id;
+} Asm;
+
+/* Resolve an id token (pass 0 registers named ids). */
+static int asm_id(Asm *A, Span t, uint32_t *out)
+{
+    uint32_t id;
+    int c = classify_id(t, &id);
+    if (c < 0) return -1;
+    if (c == 0) {
+        if (A->pass == 0 && id > A->max_explicit) A->max_explicit = id;
+    } else {
+        int k = namemap_get(&A->names, t, A->pass == 0);
+        uint64_t fresh = A->max_explicit + 1 + (uint64_t)k;
+        if (A->pass > 0 && fresh > 0xffffffffull) return -1;
+        id = (uint32_t)fresh;
+    }
+    if (A->pass == 2 && id > A->max_id) A->max_id = id;
+    *out = id;
     return 0;
 }
 
 static int parse_enum_tok(const EnumKind *k, Span t, uint32_t *v)
 {
-    uint64_t u;
-    if (parse_u64(t, &u) == 0) { *v = (uint32_t)u; return 0; }
+    if (parse_u32(t, v) == 0) return 0;
     if (!k->is_bits) {
         for (int i = 0; i < k->n; i++)
             if (strlen(k->e[i].name) == t.n && strncmp(k->e[i].name, t.s, t.n) == 0) { *v = k->e[i].value; return 0; }
@@ -1147,49 +1310,55 @@ static int parse_enum_tok(const EnumKind *k, Span t, uint32_t *v)
     if (t.n == 4 && strncmp(t.s, "None", 4) == 0) { *v = 0; return 0; }
     uint32_t acc = 0;
     size_t i = 0;
-    while (i < t.n) {
+    for (;;) {
         size_t b = i;
         while (i < t.n && t.s[i] != '|') i++;
         int ok = 0;
         for (int j = 0; j < k->n; j++)
             if (strlen(k->e[j].name) == i - b && strncmp(k->e[j].name, t.s + b, i - b) == 0) { acc |= k->e[j].value; ok = 1; }
         if (!ok) return -1;
-        i++;
+        if (i == t.n) break;
+        i++;                     /* past '|': a name must follow */
     }
     *v = acc;
     return 0;
 }
 
-typedef struct { uint8_t is_float; uint8_t width; } TypeInfo;
-typedef struct { Span *tk; int nt, ti; Words *W; TypeInfo *types; uint32_t ntypes; uint32_t rtype; uint32_t max_id; } Asm;
-
 static int asm_spec(Asm *A, const char *spec);
+
+static TypeDecl type_of(Asm *A, uint32_t id)
+{
+    for (int i = 0; i < A->ntypes; i++)
+        if (A->types[i].id == id) return A->types[i];
+    TypeDecl d = {id, 0, 32};
+    return d;
+}
 
 static int asm_one(Asm *A, const char *tok, size_t len)
 {
     Span t = A->tk[A->ti];
     if (len == 1 && tok[0] == 'I') {
-        uint32_t id; if (parse_id(t, &id)) return -1;
-        if (id > A->max_id) A->max_id = id;
+        uint32_t id; if (asm_id(A, t, &id)) return -1;
         put_word(A->W, id); A->ti++; return 0;
     }
-    if (len == 1 && tok[0] == 'L') { uint64_t v; if (parse_u64(t, &v)) return -1; put_word(A->W, (uint32_t)v); A->ti++; return 0; }
+    if (len == 1 && tok[0] == 'L') { uint32_t v; if (parse_u32(t, &v)) return -1; put_word(A->W, v); A->ti++; return 0; }
     if (len == 1 && tok[0] == 'S') { if (put_string_tok(A->W, t)) return -1; A->ti++; return 0; }
     if (len == 1 && tok[0] == 'C') {
-        TypeInfo ty = {0, 32};
-        if (A->rtype < A->ntypes) ty = A->types[A->rtype];
         if (A->nt - A->ti >= 2) {           /* three or more words print one per token */
-            while (A->ti < A->nt) { uint64_t v; if (parse_u64(A->tk[A->ti], &v)) return -1; put_word(A->W, (uint32_t)v); A->ti++; }
+            while (A->ti < A->nt) { uint32_t v; if (parse_u32(A->tk[A->ti], &v)) return -1; put_word(A->W, v); A->ti++; }
             return 0;
         }
+        TypeDecl ty = type_of(A, A->rtype);
         uint64_t v;
-        if (parse_u64(t, &v) == 0) {
+        if (parse_dec(t.s, t.n, ~0ull, &v) == 0) {
             put_word(A->W, (uint32_t)v);
             if (ty.width == 64 || v > 0xffffffffull) put_word(A->W, (uint32_t)(v >> 32));
         } else {
-            char b[64]; if (t.n >= sizeof b) return -1;
+            if (!is_float_literal(t)) return -1;
+            char *b = (char *)malloc(t.n + 1);
             memcpy(b, t.s, t.n); b[t.n] = 0;
             double d = strtod(b, NULL);
+            free(b);
             if (ty.width == 64) { uint64_t u; memcpy(&u, &d, 8); put_word(A->W, (uint32_t)u); put_word(A->W, (uint32_t)(u >> 32)); }
             else { float f = (float)d; uint32_t u; memcpy(&u, &f, 4); put_word(A->W, u); }
         }
@@ -1238,91 +1407,162 @@ static int asm_spec(Asm *A, const char *spec)
     return 0;
 }
 
-/* Assemble text into out[]. Header comment lines give version, generator,
- * bound and schema; without a bound line the bound is 1 + the largest id.
- * Returns the number of words, or -(line number) on a parse error. */
+typedef struct { uint32_t version, generator, bound, schema; int have_bound; } AsmHeader;
+
+/* digits of the given base from s[*i], at least one, value <= max */
+static int scan_num(const char *s, size_t n, size_t *i, int base, uint64_t max, uint64_t *v)
+{
+    size_t b = *i;
+    uint64_t a = 0;
+    while (*i < n) {
+        int d = hexval(s[*i]);
+        if (d < 0 || d >= base) break;
+        a = a * (uint64_t)base + (uint64_t)d;
+        if (a > max) return -1;
+        (*i)++;
+    }
+    if (*i == b) return -1;
+    *v = a;
+    return 0;
+}
+
+static int has_prefix(const char *s, size_t n, const char *p, size_t *i)
+{
+    size_t k = strlen(p);
+    if (n < k || strncmp(s, p, k) != 0) return 0;
+    *i = k;
+    return 1;
+}
+
+static void header_comment(const char *s, size_t n, AsmHeader *H)
+{
+    size_t i;
+    uint64_t a, c;
+    if (has_prefix(s, n, "; Version: ", &i)) {
+        if (scan_num(s, n, &i, 10, 255, &a) == 0 && i < n && s[i] == '.') {
+            i++;
+            if (scan_num(s, n, &i, 10, 255, &c) == 0 && i == n) H->version = (uint32_t)((a << 16) | (c << 8));
+        }
+    } else if (has_prefix(s, n, "; Generator: 0x", &i)) {
+        if (scan_num(s, n, &i, 16, 0xffffffffull, &a) == 0 && i == n) H->generator = (uint32_t)a;
+    } else if (has_prefix(s, n, "; Bound: ", &i)) {
+        if (scan_num(s, n, &i, 10, 0xffffffffull, &a) == 0 && i == n) { H->bound = (uint32_t)a; H->have_bound = 1; }
+    } else if (has_prefix(s, n, "; Schema: ", &i)) {
+        if (scan_num(s, n, &i, 10, 0xffffffffull, &a) == 0 && i == n) H->schema = (uint32_t)a;
+    }
+}
+
+/* One instruction line. Returns 0, or -1 when the line does not parse. */
+static int asm_line(Asm *A, const char *s, size_t n, Span *toks)
+{
+    int nt = tokenize(s, n, toks);
+    if (nt <= 0) return -1;
+    int ti = 0;
+    Span rid_tok = {0, 0, 0};
+    int has_rid_tok = 0;
+    if (nt >= 3 && toks[0].s[0] == '%' && toks[1].n == 1 && toks[1].s[0] == '=') {
+        rid_tok = toks[0]; has_rid_tok = 1; ti = 2;
+    }
+    Span nm = toks[ti++];
+    Words *W = A->W;
+    int64_t start = W->n;
+    put_word(W, 0);
+    const OpInfo *oi = find_op_name(nm.s, nm.n);
+    uint32_t opn;
+    if (oi) opn = oi->op;
+    else {
+        uint64_t v;
+        if (nm.n < 3 || strncmp(nm.s, "Op", 2) != 0 || parse_dec(nm.s + 2, nm.n - 2, 0xffff, &v)) return -1;
+        opn = (uint32_t)v;
+    }
+    if (!oi || (ti < nt && is_raw_word(toks[ti]))) {
+        if (has_rid_tok) return -1;
+        for (; ti < nt; ti++) {
+            if (!is_raw_word(toks[ti])) return -1;
+            uint32_t v = 0;
+            for (int k = 2; k < 10; k++) v = (v << 4) | (uint32_t)hexval(toks[ti].s[k]);
+            put_word(W, v);
+        }
+    } else {
+        A->tk = toks; A->nt = nt; A->ti = ti; A->rtype = 0;
+        /* ids resolve in text order: the result id comes first */
+        uint32_t rid = 0;
+        if (has_rid_tok && asm_id(A, rid_tok, &rid)) return -1;
+        if (oi->rtype) {
+            uint32_t ty;
+            if (A->ti >= nt || asm_id(A, toks[A->ti], &ty)) return -1;
+            put_word(W, ty); A->rtype = ty; A->ti++;
+        }
+        if (oi->rid) { if (!has_rid_tok) return -1; put_word(W, rid); }
+        else if (has_rid_tok) return -1;
+        if (asm_spec(A, oi->operands)) return -1;
+        if (A->ti != nt) return -1;
+        if (A->pass == 1 && (oi->op == 21 || oi->op == 22)) {
+            /* a type declaration: the first one of each id counts */
+            int seen = 0;
+            for (int i = 0; i < A->ntypes; i++) seen |= A->types[i].id == rid;
+            uint32_t width;
+            if (!seen && parse_u32(toks[A->nt - (oi->op == 21 ? 2 : 1)], &width) == 0) {
+                if (A->ntypes == A->captypes) {
+                    A->captypes = A->captypes ? 2 * A->captypes : 16;
+                    A->types = (TypeDecl *)realloc(A->types, sizeof(TypeDecl) * A->captypes);
+                }
+                TypeDecl d = {rid, (uint8_t)(oi->op == 22), (uint8_t)(width == 64 ? 64 : 32)};
+                A->types[A->ntypes++] = d;
+            }
+        }
+    }
+    if (W->n - start > 65535) return -1;
+    if (start < W->cap) W->out[start] = ((uint32_t)(W->n - start) << 16) | opn;
+    return 0;
+}
+
+/* Assemble text into out[] (cap words). Returns the number of words (which
+ * may exceed cap: call again with a larger buffer), or -(line number) of the
+ * first line that does not parse. */
 int64_t orc_assemble(const char *text, int64_t len, uint32_t *out, int64_t cap)
 {
     Words W = {out, 0, cap};
-    uint32_t version = 0x00010200u, generator = 0, bound = 0, schema = 0;
-    int have_bound = 0;
-    for (int i = 0; i < 5; i++) put_word(&W, 0);
-    uint32_t ntypes = 1u << 22;
-    TypeInfo *types = (TypeInfo *)calloc(ntypes, sizeof(TypeInfo));
-    Span *toks = (Span *)malloc(sizeof(Span) * 70000);
-    uint32_t max_id = 0;
-    int64_t i = 0, line = 0;
-    while (i < len) {
-        int64_t b = i;
-        while (i < len && text[i] != '\n') i++;
-        const char *s = text + b;
-        size_t n = (size_t)(i - b);
-        i++; line++;
-        if (n == 0) continue;
-        if (s[0] == ';') {
-            unsigned a, c;
-            char tmp[128]; size_t k = n < 127 ? n : 127; memcpy(tmp, s, k); tmp[k] = 0;
-            if (sscanf(tmp, "; Version: %u.%u", &a, &c) == 2) version = (a << 16) | (c << 8);
-            else if (sscanf(tmp, "; Generator: 0x%x", &a) == 1) generator = a;
-            else if (sscanf(tmp, "; Bound: %u", &a) == 1) { bound = a; have_bound = 1; }
-            else if (sscanf(tmp, "; Schema: %u", &a) == 1) schema = a;
-            continue;
-        }
-        int nt = tokenize(s, n, toks, 70000);
-        if (nt <= 0) goto fail;
-        int ti = 0;
-        uint32_t rid_v = 0; int has_rid_tok = 0;
-        if (nt >= 3 && toks[0].s[0] == '%' && toks[1].n == 1 && toks[1].s[0] == '=') {
-            if (parse_id(toks[0], &rid_v)) goto fail;
-            has_rid_tok = 1; ti = 2;
-        }
-        Span nm = toks[ti++];
-        int64_t start = W.n;
-        put_word(&W, 0);
-        const OpInfo *oi = find_op_name(nm.s, nm.n);
-        uint32_t opn;
-        if (oi) opn = oi->op;
-        else {
-            if (nm.n < 3 || strncmp(nm.s, "Op", 2) != 0) goto fail;
-            Span d = {nm.s + 2, nm.n - 2}; uint64_t v;
-            if (parse_u64(d, &v)) goto fail;
-            opn = (uint32_t)v;
-        }
-        if (!oi || (ti < nt && is_raw_word(toks[ti]))) {
-            if (has_rid_tok) goto fail;
-            for (; ti < nt; ti++) {
-                if (!is_raw_word(toks[ti])) goto fail;
-                put_word(&W, (uint32_t)strtoul(toks[ti].s, NULL, 16));
+    uint32_t scratch;
+    Words W0 = {&scratch, 0, 0};
+    AsmHeader H = {0x00010200u, 0, 0, 0, 0};
+    Span *toks = (Span *)malloc(sizeof(Span) * (size_t)(len / 2 + 2));
+    Asm A;
+    memset(&A, 0, sizeof A);
+    int64_t result = 0;
+    /* pass 0 registers the named ids in order of first appearance and finds
+     * the largest explicit id; pass 1, with every id now final, records the
+     * first type declaration of each id; pass 2 writes the words */
+    for (int pass = 0; pass < 3 && result == 0; pass++) {
+        A.pass = pass;
+        W0.n = 0;
+        A.W = pass == 2 ? &W : &W0;
+        if (pass == 2) for (int i = 0; i < 5; i++) put_word(&W, 0);
+        int64_t i = 0, line = 0;
+        while (i < len) {
+            int64_t b = i;
+            while (i < len && text[i] != '\n') i++;
+            const char *s = text + b;
+            size_t n = (size_t)(i - b);
+            i++; line++;
+            if (n == 0) continue;
+            if (s[0] == ';') {
+                if (pass == 2) header_comment(s, n, &H);
+                continue;
             }
-        } else {
-            Asm A = {toks, nt, ti, &W, types, ntypes, 0, max_id};
-            if (oi->rtype) {
-                uint32_t ty; if (A.ti >= nt || parse_id(toks[A.ti], &ty)) goto fail;
-                put_word(&W, ty); A.rtype = ty; A.ti++;
-                if (ty > A.max_id) A.max_id = ty;
-            }
-            if (oi->rid) { if (!has_rid_tok) goto fail; put_word(&W, rid_v); if (rid_v > A.max_id) A.max_id = rid_v; }
-            else if (has_rid_tok) goto fail;
-            if (asm_spec(&A, oi->operands)) goto fail;
-            if (A.ti != nt) goto fail;
-            max_id = A.max_id;
-            /* remember float/int and width of type ids for later OpConstant values */
-            if ((oi->op == 21 || oi->op == 22) && rid_v < ntypes && start + 2 < W.cap && W.n > start + 2) {
-                types[rid_v].is_float = (oi->op == 22);
-                types[rid_v].width = (uint8_t)W.out[start + 2];
-            }
+            if (asm_line(&A, s, n, toks)) { result = -line; break; }
         }
-        if (start < W.cap) W.out[start] = ((uint32_t)(W.n - start) << 16) | opn;
     }
-    free(types); free(toks);
-    if (5 <= W.cap) {
-        out[0] = ORC_MAGIC; out[1] = version; out[2] = generator;
-        out[3] = have_bound ? bound : max_id + 1; out[4] = schema;
+    if (result == 0) {
+        result = W.n;
+        if (5 <= W.cap) {
+            out[0] = ORC_MAGIC; out[1] = H.version; out[2] = H.generator;
+            out[3] = H.have_bound ? H.bound : (uint32_t)(A.max_id + 1);
+            out[4] = H.schema;
+        }
     }
-    return W.n;
-fail:
-    free(types); free(toks);
-    return -line;
+    free(toks); free(A.names.names); free(A.names.slot); free(A.types);
+    return result;
 }
 
 /* ------------------------------------------------------------------ */
