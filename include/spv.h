@@ -306,6 +306,72 @@ int spv_disassemble_batch(const spv_batch *batch, const spv_table *table, const 
                           void *workspace, size_t workspace_bytes, int64_t arena_words, spv_stream_t stream);
 
 /*
+ * Assembler: text back to words (section 3.4.4, Dis/Assembler), for every
+ * module of a batch at once; the inverse of spv_disassemble_batch, with the
+ * paper's hash table from id names to ids.
+ *
+ * The text form, per module (lines end at '\n'; a final '\n' does not start
+ * another line; lines are numbered from 1 in each module):
+ *   - an empty line is skipped;
+ *   - a line starting with ';' is a comment; exactly "; Version: A.B"
+ *     (A, B <= 255), "; Generator: 0xH", "; Bound: N" and "; Schema: N"
+ *     (values < 2^32, nothing after them) set header words, the last such
+ *     line of each field winning;
+ *   - any other line is one instruction: tokens split by spaces, a token that
+ *     starts with '"' running to the next '"' not escaped by '\' (an unclosed
+ *     one is an error): "[%r =] OpName operands" in the operand order of the
+ *     opcode table (result type first), or "Op<decimal> 0xHHHHHHHH ..." (raw
+ *     words; also after a known name when its first operand token is one).
+ * Ids: "%<digits>" and "%<name>_<digits>" are the id <digits> (< 2^32); any
+ * other "%<name>" is a named id: a module's distinct names get the ids M+1,
+ * M+2, ... in order of first appearance in its text, M its largest explicit
+ * id (0 if none). Literals are decimal, < 2^32. Strings: "\xHH" is the byte
+ * HH, '\' before any other byte is that byte. Enumerants: the name or a
+ * decimal number; bit enums also "None" and "A|B". An OpConstant value of two
+ * or more tokens is one word per token; of one token it is a decimal integer
+ * (< 2^64) or a float literal ([+-] then inf, nan, C99 hexadecimal or
+ * decimal), as wide as the result type: the first OpTypeInt / OpTypeFloat of
+ * the module defining that id, else 32-bit. Float literals round exactly to
+ * double, to nearest even; a 32-bit constant is that double rounded again to
+ * float. An instruction has at most 65535 words.
+ * Each module's words: magic, version (default 1.2), generator (0), bound
+ * (the Bound line, else the largest id + 1), schema (0), then one
+ * instruction per instruction line.
+ *
+ * text: device, text_bytes bytes; module m is text[text_off[m] ..
+ * text_off[m+1]) (text_off: device, n_modules + 1 entries, non-decreasing,
+ * text_off[n_modules] <= text_bytes; otherwise every module gets
+ * SPV_ASM_BAD_OFFSETS). Module m's words go to words[word_off[m] ..
+ * word_off[m+1]) (word_off: device, n_modules + 1 entries, always filled); a
+ * module that is not SPV_ASM_OK has no words. No word at or past
+ * words_capacity is written: when word_off[n_modules] exceeds it, call again
+ * with a larger buffer. asm_status (device, n_modules) gets spv_asm_status
+ * codes; asm_err_line (device, may be NULL) the first bad line of a
+ * SPV_ASM_SYNTAX module, else -1.
+ * line_capacity / name_capacity bound the lines and the named-id occurrences
+ * the workspace holds (0: text_bytes / 16 + n_modules + 64 lines and
+ * text_bytes / 32 + 64 occurrences); modules past them get SPV_ASM_CAPACITY
+ * and spv_asm_required then tells what the call needed.
+ */
+typedef enum spv_asm_status {
+    SPV_ASM_OK = 0,
+    SPV_ASM_SYNTAX = 1,         /* a line that does not parse (asm_err_line) */
+    SPV_ASM_CAPACITY = 2,       /* the workspace's line or name capacity is too small */
+    SPV_ASM_BAD_OFFSETS = 3     /* text_off decreasing or past text_bytes */
+} spv_asm_status;
+
+size_t spv_asm_workspace_bytes(int32_t n_modules, uint64_t text_bytes, int64_t line_capacity, int64_t name_capacity);
+
+int spv_assemble_batch(const char *text, uint64_t text_bytes, const uint64_t *text_off, int32_t n_modules,
+                       uint32_t *words, int64_t words_capacity, int64_t *word_off, uint32_t *asm_status,
+                       int64_t *asm_err_line, void *workspace, size_t workspace_bytes, int64_t line_capacity,
+                       int64_t name_capacity, spv_stream_t stream);
+
+/* Lines and named-id occurrences the last spv_assemble_batch on this
+ * workspace needed (synchronous: waits for that call). */
+int spv_asm_required(const void *workspace, int64_t *lines, int64_t *names);
+
+/*
  * Serving: continuous batching of modules that arrive one by one, as a JIT
  * backend produces them (the paper's use case, section 4). A server owns a
  * device pool and a pinned host pool. Submitted modules wait in a queue; a

@@ -97,6 +97,12 @@ def load():
     lib.spv_autotune_batch.restype = ctypes.c_int
     lib.spv_autotune_batch.argtypes = [BP, TP, P, P, ctypes.c_int, P, P, sz, ctypes.c_int, CP,
                                        ctypes.POINTER(ctypes.c_float), P]
+    lib.spv_asm_workspace_bytes.restype = sz
+    lib.spv_asm_workspace_bytes.argtypes = [i32, ctypes.c_uint64, i64, i64]
+    lib.spv_assemble_batch.restype = ctypes.c_int
+    lib.spv_assemble_batch.argtypes = [P, ctypes.c_uint64, P, i32, P, i64, P, P, P, P, sz, i64, i64, P]
+    lib.spv_asm_required.restype = ctypes.c_int
+    lib.spv_asm_required.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     _lib = lib
     return lib
 
@@ -385,6 +391,71 @@ def disassemble(words, mod_off, table, *, inline_names=True, header=True, text=N
             return text[:total], text_off, dis_status[:m]
         text = torch.empty(total, dtype=torch.uint8, device=dev)
     raise SpvError("text buffer sizing failed")
+
+
+# ---------------------------------------------------------------------------
+# assembler
+# ---------------------------------------------------------------------------
+ASM_STATUS = ["OK", "SYNTAX", "CAPACITY", "BAD_OFFSETS"]
+
+
+def spv_asm_workspace_bytes(n_modules, text_bytes, line_capacity=0, name_capacity=0):
+    return load().spv_asm_workspace_bytes(n_modules, text_bytes, line_capacity, name_capacity)
+
+
+def spv_assemble_batch(text, text_bytes, text_off, n_modules, words, words_capacity, word_off, asm_status,
+                       asm_err_line, workspace, ws_bytes, line_capacity, name_capacity, stream):
+    return load().spv_assemble_batch(text, text_bytes, text_off, n_modules, words, words_capacity, word_off,
+                                     asm_status, asm_err_line, workspace, ws_bytes, line_capacity, name_capacity,
+                                     stream)
+
+
+def spv_asm_required(workspace):
+    lines, names = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().spv_asm_required(workspace, ctypes.byref(lines), ctypes.byref(names)), "spv_asm_required")
+    return int(lines.value), int(names.value)
+
+
+class AsmWorkspace:
+    def __init__(self, n_modules, text_bytes, device, line_capacity=0, name_capacity=0):
+        self.bytes = spv_asm_workspace_bytes(n_modules, text_bytes, line_capacity, name_capacity)
+        self.buf = torch.empty(max(1, self.bytes), dtype=torch.uint8, device=device)
+        self.line_capacity, self.name_capacity = line_capacity, name_capacity
+
+
+def assemble(text, text_off, *, words=None, workspace=None, stream=None, line_capacity=0, name_capacity=0,
+             sync=True):
+    """Words of every module's text (device uint8 text, device int64
+    text_off of n + 1 entries). With sync (default) the call waits for the
+    stream, grows the word buffer and the workspace capacities when needed,
+    and returns (words int32 tensor trimmed to its size, word_off int64,
+    asm_status int32, asm_err_line int64)."""
+    m = text_off.numel() - 1
+    dev = text.device
+    if words is None:
+        words = torch.empty(max(16, text.numel() // 2 + 8 * m), dtype=torch.int32, device=dev)
+    word_off = torch.empty(m + 1, dtype=torch.int64, device=dev)
+    status = torch.empty(max(1, m), dtype=torch.int32, device=dev)
+    err = torch.empty(max(1, m), dtype=torch.int64, device=dev)
+    for _ in range(4):
+        if workspace is None:
+            workspace = AsmWorkspace(m, text.numel(), dev, line_capacity, name_capacity)
+        rc = spv_assemble_batch(_ptr(text), text.numel(), _ptr(text_off), m, _ptr(words), words.numel(),
+                                _ptr(word_off), _ptr(status), _ptr(err), _ptr(workspace.buf), workspace.bytes,
+                                workspace.line_capacity, workspace.name_capacity, _stream(stream))
+        _check(rc, "spv_assemble_batch")
+        if not sync:
+            return words, word_off, status[:m], err[:m]
+        if m and bool((status[:m] == 2).any()):           # CAPACITY: size the workspace to what was needed
+            lines, names = spv_asm_required(_ptr(workspace.buf))
+            line_capacity, name_capacity = lines + 1, names + 1
+            workspace = None
+            continue
+        total = int(word_off[-1].item())
+        if total <= words.numel():
+            return words[:total], word_off, status[:m], err[:m]
+        words = torch.empty(total, dtype=torch.int32, device=dev)
+    raise SpvError("assembler buffer sizing failed")
 
 
 # ---------------------------------------------------------------------------
