@@ -525,6 +525,36 @@ def main():
                   "ms": lay, "rows_per_s": N / (lay * 1e-3), "achieved_gbs": (2 * N + 8 * M) / (lay * 1e-3) / 1e9,
                   "all_clean": bool((lst == 0).all().item())}
 
+    # assembler (spv_assemble_batch): the step's own text back to words, which
+    # must be the input words; reads the text (L bytes), writes 4 W bytes
+    aws = spvgpu.AsmWorkspace(M, Ltext, dev)
+    a_words = torch.empty_like(words)
+    a_text = text_buf[:Ltext]
+    spvgpu.assemble(a_text, text_off, words=a_words, workspace=aws)
+    asm_ms = []
+    spvgpu.profile_enable(True)
+    for k in range(6):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if flush is not None:
+            flush.zero_()
+        a.record(stream)
+        _, a_off, a_st, _ = spvgpu.assemble(a_text, text_off, words=a_words, workspace=aws, sync=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k:
+            asm_ms.append(a.elapsed_time(b))
+    aprof = spvgpu.profile_read()
+    spvgpu.profile_enable(False)
+    asm_t = float(np.median(asm_ms))
+    asm_kernels = {k: {"launches": v[0], "ms_per_call": v[1] / 6} for k, v in
+                   sorted(aprof.items(), key=lambda kv: -kv[1][1])[:8]}
+    asm_leg = {"scope": "the step's disassembly text back to words (named ids, types, constants, headers)",
+               "ms": asm_t, "text_gbs": Ltext / (asm_t * 1e-3) / 1e9,
+               "achieved_gbs": (Ltext + 4 * W) / (asm_t * 1e-3) / 1e9,
+               "round_trip_exact": bool(torch.equal(a_words, words)) and bool(torch.equal(a_off, mod_off))
+               and bool((a_st == 0).all().item()),
+               "kernels": asm_kernels}
+
     # batched vs per-module launches (decode+validate+encode, same exact output)
     cmp = None
     if not args.no_per_module and world == 1:
@@ -576,6 +606,7 @@ def main():
         "e2e": e2e,
         "batched_vs_per_module": cmp,
         "layout": layout_leg,
+        "assemble": asm_leg,
         "serve": serve,
         "clocks": clk,
         "gpu_launches": launches,

@@ -477,8 +477,9 @@ struct AsmMod {
     unsigned long long distinct;    // distinct names
 };
 
-// line flags
-enum : uint8_t { LF_TYPEDECL = 1, LF_CONST1 = 2, LF_W64 = 4 };
+// line flags; LF_SLOT: the line's final words (at most SLOT_WORDS) are in its slot
+enum : uint8_t { LF_TYPEDECL = 1, LF_CONST1 = 2, LF_W64 = 4, LF_SLOT = 8 };
+constexpr int SLOT_WORDS = 8;
 
 struct AsmP {
     const uint8_t *text;
@@ -497,6 +498,7 @@ struct AsmP {
     int32_t *lmod;
     uint32_t *lw, *lnm;
     uint8_t *lfl;
+    uint32_t *lslot;                // SLOT_WORDS words per line
     unsigned long long *lwo, *occ_off;
     long long occ_cap;
     unsigned long long *occ_slot, *occ_pos;
@@ -846,9 +848,10 @@ struct Walk {
     bool w64;                       // the constant's type is 64 bits wide (CONST, EMIT)
     // occurrences of this line start here (NAMES, TYPES, CONST, EMIT)
     unsigned long long occ;
-    // output (EMIT)
+    // output (EMIT); the line's slot (MEASURE, CONST)
     uint32_t *out;
     long long out_at, out_cap;
+    uint32_t *slot;
 };
 
 template <int MODE>
@@ -857,6 +860,9 @@ __device__ __forceinline__ void put(Walk &w, uint32_t v)
     if (MODE == M_EMIT) {
         const long long at = w.out_at + w.words;
         if (at < w.out_cap) w.out[at] = v;
+    }
+    if (MODE == M_MEASURE || MODE == M_CONST) {
+        if (w.words < SLOT_WORDS) w.slot[w.words] = v;
     }
     w.words++;
 }
@@ -965,7 +971,7 @@ __device__ bool take_string(Walk &w, const Tok &t)
         } else {
             i++;
         }
-        if (MODE == M_EMIT) acc |= ch << (8 * k);
+        if (MODE == M_EMIT || MODE == M_MEASURE || MODE == M_CONST) acc |= ch << (8 * k);
         if (++k == 4) { put<MODE>(w, acc); acc = 0; k = 0; }
     }
     put<MODE>(w, acc);
@@ -1001,11 +1007,10 @@ __device__ bool take_ctx(Walk &w, const Tok &t)
         if (w.w64 || (v >> 32)) put<MODE>(w, (uint32_t)(v >> 32));
         return true;
     }
-    if (MODE != M_EMIT) {
+    if (MODE != M_EMIT && MODE != M_CONST) {
         if (!float_literal<false>(s, t.n, nullptr)) return false;
         if (MODE == M_MEASURE) w.flags |= LF_CONST1;
         put<MODE>(w, 0);
-        if (MODE == M_CONST && w.w64) put<MODE>(w, 0);
         return true;
     }
     uint64_t bits;
@@ -1106,28 +1111,59 @@ __device__ bool take_operand(Walk &w, uint8_t code)
     }
 }
 
+// The start of an instruction line: the first token, whether it is a
+// "%r =" result id, the opcode-name token and its opcode (-1 if no name of
+// the table). False if the line has no token.
+struct Prefix { Tok t0, nm; int op; bool has_rid; };
+__device__ bool line_prefix(const uint8_t *s, uint32_t n, Prefix &p)
+{
+    uint32_t i = 0;
+    if (!next_tok(s, n, i, p.t0)) return false;
+    p.has_rid = false;
+    uint32_t k = i;
+    Tok t1;
+    if (s[p.t0.b] == '%' && next_tok(s, n, k, t1) && t1.n == 1 && s[t1.b] == '=' && more_toks(s, n, k)) {
+        p.has_rid = true;
+        next_tok(s, n, k, p.nm);
+    } else {
+        p.nm = p.t0;
+    }
+    p.op = find_op(s + p.nm.b, p.nm.n);
+    return true;
+}
+// packed in 64 bits for lines whose prefix positions are below 2048
+__device__ __forceinline__ unsigned long long pack_prefix(const Prefix &p, bool ok)
+{
+    if (!ok) return 1ull << 10;                        // no token
+    if ((p.t0.b | p.t0.n | p.nm.b | p.nm.n) >= 2048u) return 0;   // not packed
+    return (unsigned long long)(p.op + 1) | ((unsigned long long)p.has_rid << 9) | (3ull << 10) |
+           ((unsigned long long)p.t0.b << 12) | ((unsigned long long)p.t0.n << 23) |
+           ((unsigned long long)p.nm.b << 34) | ((unsigned long long)p.nm.n << 45);
+}
+__device__ __forceinline__ void unpack_prefix(unsigned long long v, Prefix &p)
+{
+    p.op = (int)(v & 511) - 1;
+    p.has_rid = (v >> 9) & 1;
+    p.t0.b = (uint32_t)(v >> 12) & 2047; p.t0.n = (uint32_t)(v >> 23) & 2047; p.t0.open = false;
+    p.nm.b = (uint32_t)(v >> 34) & 2047; p.nm.n = (uint32_t)(v >> 45) & 2047; p.nm.open = false;
+}
+
 // Walk one instruction line. Returns 0 or E_SYNTAX. In EMIT, words_total is
-// the line's word count (known from the scan).
+// the line's word count (known from the scan). pre: the line's prefix when
+// already known.
 template <int MODE>
-__device__ uint32_t walk_line(Walk &w, long long line, uint32_t words_total)
+__device__ uint32_t walk_line(Walk &w, long long line, uint32_t words_total, const Prefix *pre = nullptr)
 {
     const uint8_t *s = w.s;
     const uint32_t n = w.n;
     w.i = 0; w.words = 0; w.named = 0; w.flags = 0; w.have_lit = false; w.first_lit = 0;
-    Tok t0, t1, nm;
-    uint32_t i = 0;
-    if (!next_tok(s, n, i, t0)) return E_SYNTAX;
-    bool has_rid = false;
-    {
-        uint32_t k = i;
-        if (s[t0.b] == '%' && next_tok(s, n, k, t1) && t1.n == 1 && s[t1.b] == '=' && more_toks(s, n, k)) {
-            has_rid = true;
-            i = k;
-        }
-    }
-    if (has_rid) next_tok(s, n, i, nm);
-    else nm = t0;
-    const int op = find_op(s + nm.b, nm.n);
+    Prefix px;
+    if (pre) px = *pre;
+    else if (!line_prefix(s, n, px)) return E_SYNTAX;
+    const Tok t0 = px.t0, nm = px.nm;
+    const bool has_rid = px.has_rid;
+    const int op = px.op;
+    uint32_t i = nm.b + nm.n;
     uint32_t opn;
     if (op >= 0) {
         opn = (uint32_t)op;
@@ -1149,7 +1185,9 @@ __device__ uint32_t walk_line(Walk &w, long long line, uint32_t words_total)
                 if (!raw_word(s + f.b, f.n, v)) return E_SYNTAX;
                 put<MODE>(w, v);
             }
-            return w.words > 65535 ? E_SYNTAX : 0;
+            if (w.words > 65535) return E_SYNTAX;
+            if (MODE == M_MEASURE || MODE == M_CONST) w.slot[0] = (w.words << 16) | opn;
+            return 0;
         }
     }
     const spvt::OpDesc &d = g_spv_tables.ops[op];
@@ -1175,6 +1213,7 @@ __device__ uint32_t walk_line(Walk &w, long long line, uint32_t words_total)
         if (MODE == M_MEASURE) w.flags |= LF_TYPEDECL;
         if (MODE == M_TYPES) type_insert(w, rid, opn == 22, w.first_lit == 64, line);
     }
+    if (MODE == M_MEASURE || MODE == M_CONST) w.slot[0] = (w.words << 16) | opn;
     return 0;
 }
 
@@ -1241,6 +1280,86 @@ __device__ __forceinline__ bool module_ready(const AsmMod &M, uint32_t need)
     return (M.flags & need) == need && M.err == ~0ull;
 }
 
+// One line in one mode. sline: the line's bytes staged in shared memory,
+// or null to read them from the text.
+template <int MODE>
+__device__ __forceinline__ void parse_line(const AsmP &P, long long l, const uint8_t *sline)
+{
+    if (MODE == M_NAMES && P.lnm[l] == 0) return;
+    if (MODE == M_TYPES && !(P.lfl[l] & LF_TYPEDECL)) return;
+    if (MODE == M_CONST && !(P.lfl[l] & LF_CONST1)) return;
+    if (MODE == M_EMIT && P.lw[l] == 0) return;
+    if (MODE == M_MEASURE) { P.lw[l] = 0; P.lnm[l] = 0; P.lfl[l] = 0; }
+    const int m = P.lmod[l];
+    AsmMod &M = P.mod[m];
+    if (MODE == M_MEASURE) {
+        if (!(M.flags & MF_FIT_LINES)) return;
+    } else {
+        if (!module_ready(M, MF_FIT_LINES | MF_FIT_OCC | MF_FIT_ARENA)) return;
+    }
+    if (MODE == M_EMIT && (P.lfl[l] & LF_SLOT)) {        // words recorded by the measuring pass
+        const long long at = P.word_off[m] + 5 + (long long)(P.lwo[l] - P.lwo[M.first_line]);
+        const uint32_t n = P.lw[l];
+        const uint4 *sl = reinterpret_cast<const uint4 *>(P.lslot + (size_t)SLOT_WORDS * l);
+        const uint4 x = sl[0], y = sl[1];
+        const uint32_t v[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+        #pragma unroll
+        for (uint32_t k = 0; k < 8; k++)
+            if (k < n && at + k < P.words_cap) P.words[at + k] = v[k];
+        return;
+    }
+    const unsigned long long q = P.ls[l];
+    const unsigned long long mend = P.text_off[m + 1];
+    unsigned long long e = l + 1 < M.end_line ? P.ls[l + 1] - 1 : mend;
+    if (l + 1 >= M.end_line && e > q && P.text[e - 1] == '\n') e--;
+    const long long rel = l - M.first_line;
+    if (e == q) return;
+    if (e - q >= (1ull << 31)) {
+        if (MODE == M_MEASURE) atomicMin(&M.err, ((unsigned long long)rel << 8) | E_SYNTAX);
+        return;
+    }
+    Walk w;
+    w.s = sline ? sline : P.text + q; w.n = (uint32_t)(e - q); w.pos = q;
+    w.M = &M; w.text = P.text; w.mod_end = P.text + mend; w.rel = rel;
+    w.arena = P.arena; w.occ_slot = P.occ_slot; w.occ_pos = P.occ_pos;
+    w.max_explicit = 0; w.w64 = false; w.occ = 0; w.out = nullptr; w.out_at = 0; w.out_cap = 0;
+    w.slot = P.lslot + (size_t)SLOT_WORDS * l;
+    if (w.s[0] == ';') {
+        if (MODE == M_MEASURE) {
+            uint32_t value;
+            const int f = header_line(w.s, w.n, value);
+            if (f >= 0) atomicMax(&M.hdr[f], ((unsigned long long)(rel + 1) << 32) | value);
+        }
+        return;
+    }
+    if (MODE != M_MEASURE) w.occ = P.occ_off[l];
+    if (MODE == M_EMIT) {
+        w.w64 = (P.lfl[l] & LF_W64) != 0;
+        w.out = P.words; w.out_cap = P.words_cap;
+        w.out_at = P.word_off[m] + 5 + (long long)(P.lwo[l] - P.lwo[M.first_line]);
+    }
+    const uint32_t st = walk_line<MODE>(w, rel, MODE == M_EMIT ? P.lw[l] : 0u);
+    if (MODE == M_MEASURE) {
+        if (st) {
+            atomicMin(&M.err, ((unsigned long long)rel << 8) | st);
+            return;
+        }
+        uint8_t fl = w.flags;
+        if (w.words <= SLOT_WORDS && w.named == 0 && !(fl & LF_CONST1)) fl |= LF_SLOT;
+        P.lw[l] = w.words;
+        P.lnm[l] = w.named;
+        P.lfl[l] = fl;
+        if (w.max_explicit > 0) atomicMax(&M.max_explicit, w.max_explicit);
+        if (w.flags & LF_TYPEDECL) atomicAdd(&M.n_types, 1u);
+    } else if (MODE == M_CONST) {
+        P.lw[l] = w.words;
+        uint8_t fl = P.lfl[l];
+        if (w.w64) fl |= LF_W64;
+        if (w.words <= SLOT_WORDS) fl |= LF_SLOT;
+        P.lfl[l] = fl;
+    }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_asm_parse(AsmP P)
 {
@@ -1248,63 +1367,166 @@ __global__ void __launch_bounds__(256) k_asm_parse(AsmP P)
     if (c.bad_offsets) return;
     const long long nl = c.n_lines < P.line_cap ? c.n_lines : P.line_cap;
     for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < nl;
-         l += (long long)gridDim.x * blockDim.x) {
-        if (MODE == M_NAMES && P.lnm[l] == 0) continue;
-        if (MODE == M_TYPES && !(P.lfl[l] & LF_TYPEDECL)) continue;
-        if (MODE == M_CONST && !(P.lfl[l] & LF_CONST1)) continue;
-        if (MODE == M_EMIT && P.lw[l] == 0) continue;
-        if (MODE == M_MEASURE) { P.lw[l] = 0; P.lnm[l] = 0; P.lfl[l] = 0; }
-        const int m = P.lmod[l];
-        AsmMod &M = P.mod[m];
-        if (MODE == M_MEASURE) {
-            if (!(M.flags & MF_FIT_LINES)) continue;
-        } else {
-            if (!module_ready(M, MF_FIT_LINES | MF_FIT_OCC | MF_FIT_ARENA)) continue;
-        }
-        const unsigned long long q = P.ls[l];
-        const unsigned long long mend = P.text_off[m + 1];
-        unsigned long long e = l + 1 < M.end_line ? P.ls[l + 1] - 1 : mend;
-        if (l + 1 >= M.end_line && e > q && P.text[e - 1] == '\n') e--;
+         l += (long long)gridDim.x * blockDim.x)
+        parse_line<MODE>(P, l, nullptr);
+}
+
+// The measuring pass by tiles of MT_LINES consecutive lines: the tile's text
+// is staged in shared memory; each line's prefix (result id, opcode name) is
+// read once, and the lines are sorted by the text shape of their opcode, so
+// that a warp takes lines that walk the same code; each line's words are
+// recorded in shared memory and written to its slot as whole 32-byte
+// sectors.
+constexpr int MT_THREADS = 256, MT_LINES = 1024, MT_TEXT = 48 * 1024, MT_KEYS = 256;
+struct MTSmem {
+    alignas(16) uint8_t text[MT_TEXT];
+    alignas(16) uint32_t slot[MT_THREADS][SLOT_WORDS];
+    unsigned long long pre[MT_LINES];    // packed prefix (0: not packed)
+    uint16_t perm[MT_LINES];
+    uint16_t len[MT_LINES];              // line length; 0xffff: longer
+    uint8_t key[MT_LINES];
+    uint32_t hist[MT_KEYS];
+};
+
+__device__ __forceinline__ void measure_line(const AsmP &P, long long l, unsigned long long q, const uint8_t *s,
+                                             uint32_t n, const Prefix *pre, uint32_t *sslot)
+{
+    const int m = P.lmod[l];
+    AsmMod &M = P.mod[m];
+    uint32_t lw = 0, lnm = 0;
+    uint8_t fl = 0;
+    if ((M.flags & MF_FIT_LINES) && n) {
         const long long rel = l - M.first_line;
-        if (e == q) continue;
-        if (e - q >= (1ull << 31)) {
-            if (MODE == M_MEASURE) atomicMin(&M.err, ((unsigned long long)rel << 8) | E_SYNTAX);
-            continue;
-        }
-        Walk w;
-        w.s = P.text + q; w.n = (uint32_t)(e - q); w.pos = q;
-        w.M = &M; w.text = P.text; w.mod_end = P.text + mend; w.rel = rel;
-        w.arena = P.arena; w.occ_slot = P.occ_slot; w.occ_pos = P.occ_pos;
-        w.max_explicit = 0; w.w64 = false; w.occ = 0; w.out = nullptr; w.out_at = 0; w.out_cap = 0;
-        if (w.s[0] == ';') {
-            if (MODE == M_MEASURE) {
-                uint32_t value;
-                const int f = header_line(w.s, w.n, value);
-                if (f >= 0) atomicMax(&M.hdr[f], ((unsigned long long)(rel + 1) << 32) | value);
-            }
-            continue;
-        }
-        if (MODE != M_MEASURE) w.occ = P.occ_off[l];
-        if (MODE == M_EMIT) {
-            w.w64 = (P.lfl[l] & LF_W64) != 0;
-            w.out = P.words; w.out_cap = P.words_cap;
-            w.out_at = P.word_off[m] + 5 + (long long)(P.lwo[l] - P.lwo[M.first_line]);
-        }
-        const uint32_t st = walk_line<MODE>(w, rel, MODE == M_EMIT ? P.lw[l] : 0u);
-        if (MODE == M_MEASURE) {
+        if (s[0] == ';') {
+            uint32_t value;
+            const int f = header_line(s, n, value);
+            if (f >= 0) atomicMax(&M.hdr[f], ((unsigned long long)(rel + 1) << 32) | value);
+        } else {
+            Walk w;
+            w.s = s; w.n = n; w.pos = q;
+            w.M = &M; w.text = P.text; w.mod_end = nullptr; w.rel = rel;
+            w.arena = P.arena; w.occ_slot = P.occ_slot; w.occ_pos = P.occ_pos;
+            w.max_explicit = 0; w.w64 = false; w.occ = 0; w.out = nullptr; w.out_at = 0; w.out_cap = 0;
+            w.slot = sslot;
+            const uint32_t st = walk_line<M_MEASURE>(w, rel, 0u, pre);
             if (st) {
                 atomicMin(&M.err, ((unsigned long long)rel << 8) | st);
+            } else {
+                fl = w.flags;
+                lw = w.words;
+                lnm = w.named;
+                if (w.words <= SLOT_WORDS && w.named == 0 && !(fl & LF_CONST1)) {
+                    fl |= LF_SLOT;
+                    uint4 *g = reinterpret_cast<uint4 *>(P.lslot + (size_t)SLOT_WORDS * l);
+                    const uint4 *a = reinterpret_cast<const uint4 *>(sslot);
+                    g[0] = a[0];
+                    g[1] = a[1];
+                }
+                if (w.max_explicit > 0) atomicMax(&M.max_explicit, w.max_explicit);
+                if (w.flags & LF_TYPEDECL) atomicAdd(&M.n_types, 1u);
+            }
+        }
+    }
+    P.lw[l] = lw;
+    P.lnm[l] = lnm;
+    P.lfl[l] = fl;
+}
+
+__global__ void __launch_bounds__(MT_THREADS, 3) k_asm_measure(AsmP P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MTSmem &S = *reinterpret_cast<MTSmem *>(smem_raw);
+    const AsmCtrl &c = *P.ctrl;
+    if (c.bad_offsets) return;
+    const long long nl = c.n_lines < P.line_cap ? c.n_lines : P.line_cap;
+    const long long ntiles = (nl + MT_LINES - 1) / MT_LINES;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long l0 = t * MT_LINES;
+        const int nt = (int)(nl - l0 < MT_LINES ? nl - l0 : MT_LINES);
+        const long long a = (long long)P.ls[l0];
+        const long long e = l0 + nt < nl ? (long long)P.ls[l0 + nt] : c.t1;
+        const long long a_al = a - (long long)(((uintptr_t)P.text + (uintptr_t)a) & 15u);
+        const long long se = e < a_al + MT_TEXT ? e : a_al + MT_TEXT;     // bytes [a, se) staged
+        for (long long k = threadIdx.x; a_al + 16 * k < se; k += MT_THREADS) {
+            const long long g = a_al + 16 * k;
+            if (g >= a && g + 16 <= se) {
+                *reinterpret_cast<uint4 *>(S.text + 16 * k) = *reinterpret_cast<const uint4 *>(P.text + g);
+            } else {
+                for (int j = 0; j < 16; j++) {
+                    const long long q = g + j;
+                    if (q >= a && q < se) S.text[16 * k + j] = P.text[q];
+                }
+            }
+        }
+        for (int i = threadIdx.x; i < MT_KEYS; i += MT_THREADS) S.hist[i] = 0;
+        __syncthreads();
+        // each line's length (up to the next line start, less its '\n'),
+        // prefix and key: 0 comments and empty lines, 1 unknown names, else
+        // the opcode's shape
+        for (int i = threadIdx.x; i < nt; i += MT_THREADS) {
+            const long long q = (long long)P.ls[l0 + i];
+            long long qe = i + 1 < nt ? (long long)P.ls[l0 + i + 1] : e;
+            if (qe > q && P.text[qe - 1] == '\n') qe--;
+            const long long n = qe - q;
+            uint32_t key = 0;
+            unsigned long long pk = 0;
+            if (n > 0 && qe <= se && S.text[q - a_al] != ';') {
+                Prefix px;
+                const bool ok = line_prefix(S.text + (q - a_al), (uint32_t)n, px);
+                pk = pack_prefix(px, ok);
+                key = !ok || px.op < 0 ? 1u : g_spv_tables.shape[px.op];
+            } else if (n > 0 && qe > se) {
+                key = 1;
+            }
+            S.len[i] = (uint16_t)(n < 0xffff ? n : 0xffff);
+            S.pre[i] = pk;
+            S.key[i] = (uint8_t)key;
+            atomicAdd(&S.hist[key], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {                      // exclusive scan of the histogram, one warp
+            const int lane = threadIdx.x;
+            uint32_t v[MT_KEYS / 32], sum = 0;
+            #pragma unroll
+            for (int k = 0; k < MT_KEYS / 32; k++) { v[k] = S.hist[lane * (MT_KEYS / 32) + k]; sum += v[k]; }
+            uint32_t x = sum;
+            #pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+                if (lane >= d) x += y;
+            }
+            uint32_t pre = x - sum;
+            #pragma unroll
+            for (int k = 0; k < MT_KEYS / 32; k++) { S.hist[lane * (MT_KEYS / 32) + k] = pre; pre += v[k]; }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nt; i += MT_THREADS) S.perm[atomicAdd(&S.hist[S.key[i]], 1u)] = (uint16_t)i;
+        __syncthreads();
+        for (int j = threadIdx.x; j < nt; j += MT_THREADS) {
+            const int i = S.perm[j];
+            const long long l = l0 + i;
+            const long long q = (long long)P.ls[l];
+            long long n = S.len[i];
+            if (n == 0xffff) {
+                long long qe = i + 1 < nt ? (long long)P.ls[l + 1] : e;
+                if (qe > q && P.text[qe - 1] == '\n') qe--;
+                n = qe - q;
+            }
+            if (n >= (1ll << 31)) {
+                AsmMod &M = P.mod[P.lmod[l]];
+                if (M.flags & MF_FIT_LINES) atomicMin(&M.err, ((unsigned long long)(l - M.first_line) << 8) | E_SYNTAX);
+                P.lw[l] = 0; P.lnm[l] = 0; P.lfl[l] = 0;
                 continue;
             }
-            P.lw[l] = w.words;
-            P.lnm[l] = w.named;
-            P.lfl[l] = w.flags;
-            if (w.max_explicit > 0) atomicMax(&M.max_explicit, w.max_explicit);
-            if (w.flags & LF_TYPEDECL) atomicAdd(&M.n_types, 1u);
-        } else if (MODE == M_CONST) {
-            P.lw[l] = w.words;
-            if (w.w64) P.lfl[l] |= LF_W64;
+            const bool staged = q + n <= se;
+            const unsigned long long pk = S.pre[i];
+            Prefix px;
+            const Prefix *pre = nullptr;
+            if (staged && (pk >> 11) & 1) { unpack_prefix(pk, px); pre = &px; }
+            measure_line(P, l, (unsigned long long)q, staged ? S.text + (q - a_al) : P.text + q, (uint32_t)n, pre,
+                         S.slot[threadIdx.x]);
         }
+        __syncthreads();
     }
 }
 
@@ -1447,7 +1669,7 @@ __global__ void k_asm_need(AsmP P)
 // workspace layout
 // ---------------------------------------------------------------------------
 struct ALayout {
-    size_t ctrl, mod, bitmap, tile_cnt, tile_off, ls, lmod, lw, lnm, lfl, lwo, occ_off, occ_slot, occ_pos, occ_first,
+    size_t ctrl, mod, bitmap, tile_cnt, tile_off, ls, lmod, lw, lnm, lfl, lslot, lwo, occ_off, occ_slot, occ_pos, occ_first,
         occ_rank, arena, msize, moff, sums, total;
     long long line_cap, occ_cap, arena_cap, tile_cap, bitmap_words, sums_cap;
 };
@@ -1481,6 +1703,7 @@ ALayout alayout(int32_t n_mod, uint64_t text_bytes, int64_t line_cap, int64_t na
     L.lw = take(4 * (size_t)L.line_cap);
     L.lnm = take(4 * (size_t)L.line_cap);
     L.lfl = take((size_t)L.line_cap);
+    L.lslot = take(4 * (size_t)SLOT_WORDS * (size_t)L.line_cap);
     L.lwo = take(8 * (size_t)(L.line_cap + 1));
     L.occ_off = take(8 * (size_t)(L.line_cap + 1));
     L.occ_slot = take(8 * (size_t)L.occ_cap);
@@ -1556,6 +1779,7 @@ extern "C" int spv_assemble_batch(const char *text, uint64_t text_bytes, const u
     P.line_cap = L.line_cap;
     P.ls = (unsigned long long *)(w + L.ls); P.lmod = (int32_t *)(w + L.lmod);
     P.lw = (uint32_t *)(w + L.lw); P.lnm = (uint32_t *)(w + L.lnm); P.lfl = (uint8_t *)(w + L.lfl);
+    P.lslot = (uint32_t *)(w + L.lslot);
     P.lwo = (unsigned long long *)(w + L.lwo); P.occ_off = (unsigned long long *)(w + L.occ_off);
     P.occ_cap = L.occ_cap;
     P.occ_slot = (unsigned long long *)(w + L.occ_slot); P.occ_pos = (unsigned long long *)(w + L.occ_pos);
@@ -1582,7 +1806,15 @@ extern "C" int spv_assemble_batch(const char *text, uint64_t text_bytes, const u
     SPV_LAUNCH("k_asm_lines", st, k_asm_lines<1><<<gt, LT_THREADS, 0, st>>>(P));
     SPV_LAUNCH("k_asm_modlines", st, k_asm_modlines<<<grid_for(32ll * n_modules, 256), 256, 0, st>>>(P));
     const int gl = grid_for(line_work, 256);
-    SPV_LAUNCH("k_asm_measure", st, k_asm_parse<M_MEASURE><<<gl, 256, 0, st>>>(P));
+    {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_asm_measure, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MTSmem));
+            attr = true;
+        }
+        const int gmt = grid_for((L.line_cap + MT_LINES - 1) / MT_LINES * MT_THREADS, MT_THREADS);
+        SPV_LAUNCH("k_asm_measure", st, k_asm_measure<<<gmt, MT_THREADS, sizeof(MTSmem), st>>>(P));
+    }
     // named-id occurrences per line, then per module
     const long long *lines_dev = &c->n_lines;
     scan(P.lnm, lines_dev, L.line_cap, sums, P.occ_off, &c->n_occ, st);
