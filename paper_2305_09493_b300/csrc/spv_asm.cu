@@ -458,6 +458,7 @@ struct AsmCtrl {
     long long n_occ;                        // named-id occurrences (may exceed the capacity)
     long long arena_used;
     long long n_mod;
+    long long n_special;                    // lines the passes after the measuring one revisit
     unsigned int bad_offsets;
     unsigned int pad;
 };
@@ -499,6 +500,7 @@ struct AsmP {
     uint32_t *lw, *lnm;
     uint8_t *lfl;
     uint32_t *lslot;                // SLOT_WORDS words per line
+    unsigned long long *special;    // lines with named ids, one-token constants, type declarations or unrecorded words
     unsigned long long *lwo, *occ_off;
     long long occ_cap;
     unsigned long long *occ_slot, *occ_pos;
@@ -1288,7 +1290,7 @@ __device__ __forceinline__ void parse_line(const AsmP &P, long long l, const uin
     if (MODE == M_NAMES && P.lnm[l] == 0) return;
     if (MODE == M_TYPES && !(P.lfl[l] & LF_TYPEDECL)) return;
     if (MODE == M_CONST && !(P.lfl[l] & LF_CONST1)) return;
-    if (MODE == M_EMIT && P.lw[l] == 0) return;
+    if (MODE == M_EMIT && ((P.lfl[l] & LF_SLOT) || P.lw[l] == 0)) return;   // k_asm_copy writes slot lines
     if (MODE == M_MEASURE) { P.lw[l] = 0; P.lnm[l] = 0; P.lfl[l] = 0; }
     const int m = P.lmod[l];
     AsmMod &M = P.mod[m];
@@ -1296,17 +1298,6 @@ __device__ __forceinline__ void parse_line(const AsmP &P, long long l, const uin
         if (!(M.flags & MF_FIT_LINES)) return;
     } else {
         if (!module_ready(M, MF_FIT_LINES | MF_FIT_OCC | MF_FIT_ARENA)) return;
-    }
-    if (MODE == M_EMIT && (P.lfl[l] & LF_SLOT)) {        // words recorded by the measuring pass
-        const long long at = P.word_off[m] + 5 + (long long)(P.lwo[l] - P.lwo[M.first_line]);
-        const uint32_t n = P.lw[l];
-        const uint4 *sl = reinterpret_cast<const uint4 *>(P.lslot + (size_t)SLOT_WORDS * l);
-        const uint4 x = sl[0], y = sl[1];
-        const uint32_t v[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-        #pragma unroll
-        for (uint32_t k = 0; k < 8; k++)
-            if (k < n && at + k < P.words_cap) P.words[at + k] = v[k];
-        return;
     }
     const unsigned long long q = P.ls[l];
     const unsigned long long mend = P.text_off[m + 1];
@@ -1336,7 +1327,7 @@ __device__ __forceinline__ void parse_line(const AsmP &P, long long l, const uin
     if (MODE == M_EMIT) {
         w.w64 = (P.lfl[l] & LF_W64) != 0;
         w.out = P.words; w.out_cap = P.words_cap;
-        w.out_at = P.word_off[m] + 5 + (long long)(P.lwo[l] - P.lwo[M.first_line]);
+        w.out_at = (long long)P.lwo[l] + (long long)P.moff[m];
     }
     const uint32_t st = walk_line<MODE>(w, rel, MODE == M_EMIT ? P.lw[l] : 0u);
     if (MODE == M_MEASURE) {
@@ -1360,15 +1351,39 @@ __device__ __forceinline__ void parse_line(const AsmP &P, long long l, const uin
     }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256) k_asm_parse(AsmP P)
+// the words the measuring (or constant) pass recorded in each line's slot
+__global__ void __launch_bounds__(256) k_asm_copy(AsmP P)
 {
     const AsmCtrl &c = *P.ctrl;
     if (c.bad_offsets) return;
     const long long nl = c.n_lines < P.line_cap ? c.n_lines : P.line_cap;
     for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < nl;
-         l += (long long)gridDim.x * blockDim.x)
-        parse_line<MODE>(P, l, nullptr);
+         l += (long long)gridDim.x * blockDim.x) {
+        if (!(P.lfl[l] & LF_SLOT)) continue;
+        const int m = P.lmod[l];
+        if (P.status[m] != SPV_ASM_OK) continue;
+        const long long at = (long long)P.lwo[l] + (long long)P.moff[m];
+        const uint32_t n = P.lw[l];
+        const uint4 *sl = reinterpret_cast<const uint4 *>(P.lslot + (size_t)SLOT_WORDS * l);
+        const uint4 x = sl[0], y = n > 4 ? sl[1] : make_uint4(0, 0, 0, 0);
+        const uint32_t v[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+        #pragma unroll
+        for (uint32_t k = 0; k < 8; k++)
+            if (k < n && at + k < P.words_cap) P.words[at + k] = v[k];
+    }
+}
+
+// the passes after the measuring one: the lines of the special list
+template <int MODE>
+__global__ void __launch_bounds__(256) k_asm_parse(AsmP P)
+{
+    const AsmCtrl &c = *P.ctrl;
+    if (c.bad_offsets) return;
+    if (MODE == M_NAMES && c.n_occ == 0) return;
+    const long long n = c.n_special < P.line_cap ? c.n_special : P.line_cap;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        parse_line<MODE>(P, (long long)P.special[k], nullptr);
 }
 
 // The measuring pass by tiles of MT_LINES consecutive lines: the tile's text
@@ -1381,20 +1396,24 @@ constexpr int MT_THREADS = 256, MT_LINES = 1024, MT_TEXT = 48 * 1024, MT_KEYS = 
 struct MTSmem {
     alignas(16) uint8_t text[MT_TEXT];
     alignas(16) uint32_t slot[MT_THREADS][SLOT_WORDS];
-    unsigned long long pre[MT_LINES];    // packed prefix (0: not packed)
+    unsigned long long pre[MT_LINES];    // packed prefix (0: not packed); then the packed outputs
+    int32_t mod[MT_LINES];
     uint16_t perm[MT_LINES];
     uint16_t len[MT_LINES];              // line length; 0xffff: longer
     uint8_t key[MT_LINES];
     uint32_t hist[MT_KEYS];
 };
 
-__device__ __forceinline__ void measure_line(const AsmP &P, long long l, unsigned long long q, const uint8_t *s,
-                                             uint32_t n, const Prefix *pre, uint32_t *sslot)
+// returns the line's packed outputs: words | named << 20 | flags << 40; the
+// largest explicit id goes to max_explicit
+__device__ __forceinline__ unsigned long long measure_line(const AsmP &P, long long l, int m, unsigned long long q,
+                                                           const uint8_t *s, uint32_t n, const Prefix *pre,
+                                                           uint32_t *sslot, uint32_t &max_explicit)
 {
-    const int m = P.lmod[l];
     AsmMod &M = P.mod[m];
     uint32_t lw = 0, lnm = 0;
     uint8_t fl = 0;
+    max_explicit = 0;
     if ((M.flags & MF_FIT_LINES) && n) {
         const long long rel = l - M.first_line;
         if (s[0] == ';') {
@@ -1422,14 +1441,12 @@ __device__ __forceinline__ void measure_line(const AsmP &P, long long l, unsigne
                     g[0] = a[0];
                     g[1] = a[1];
                 }
-                if (w.max_explicit > 0) atomicMax(&M.max_explicit, w.max_explicit);
+                max_explicit = w.max_explicit;
                 if (w.flags & LF_TYPEDECL) atomicAdd(&M.n_types, 1u);
             }
         }
     }
-    P.lw[l] = lw;
-    P.lnm[l] = lnm;
-    P.lfl[l] = fl;
+    return (unsigned long long)lw | ((unsigned long long)lnm << 20) | ((unsigned long long)fl << 40);
 }
 
 __global__ void __launch_bounds__(MT_THREADS, 3) k_asm_measure(AsmP P)
@@ -1480,6 +1497,7 @@ __global__ void __launch_bounds__(MT_THREADS, 3) k_asm_measure(AsmP P)
             }
             S.len[i] = (uint16_t)(n < 0xffff ? n : 0xffff);
             S.pre[i] = pk;
+            S.mod[i] = P.lmod[l0 + i];
             S.key[i] = (uint8_t)key;
             atomicAdd(&S.hist[key], 1u);
         }
@@ -1512,19 +1530,46 @@ __global__ void __launch_bounds__(MT_THREADS, 3) k_asm_measure(AsmP P)
                 if (qe > q && P.text[qe - 1] == '\n') qe--;
                 n = qe - q;
             }
+            const int m = S.mod[i];
+            uint32_t mx = 0;
+            unsigned long long out = 0;
             if (n >= (1ll << 31)) {
-                AsmMod &M = P.mod[P.lmod[l]];
+                AsmMod &M = P.mod[m];
                 if (M.flags & MF_FIT_LINES) atomicMin(&M.err, ((unsigned long long)(l - M.first_line) << 8) | E_SYNTAX);
-                P.lw[l] = 0; P.lnm[l] = 0; P.lfl[l] = 0;
-                continue;
+            } else {
+                const bool staged = q + n <= se;
+                const unsigned long long pk = S.pre[i];
+                Prefix px;
+                const Prefix *pre = nullptr;
+                if (staged && (pk >> 11) & 1) { unpack_prefix(pk, px); pre = &px; }
+                out = measure_line(P, l, m, (unsigned long long)q, staged ? S.text + (q - a_al) : P.text + q,
+                                   (uint32_t)n, pre, S.slot[threadIdx.x], mx);
             }
-            const bool staged = q + n <= se;
-            const unsigned long long pk = S.pre[i];
-            Prefix px;
-            const Prefix *pre = nullptr;
-            if (staged && (pk >> 11) & 1) { unpack_prefix(pk, px); pre = &px; }
-            measure_line(P, l, (unsigned long long)q, staged ? S.text + (q - a_al) : P.text + q, (uint32_t)n, pre,
-                         S.slot[threadIdx.x]);
+            S.pre[i] = out;
+            if (mx) atomicMax(&P.mod[m].max_explicit, mx);
+            // lines that a later pass revisits, appended (one atomic per warp)
+            const uint32_t ofl = (uint32_t)(out >> 40), olw = (uint32_t)(out & 0xfffff);
+            const bool sp = (ofl & (LF_CONST1 | LF_TYPEDECL)) || ((out >> 20) & 0xfffff) || (olw && !(ofl & LF_SLOT));
+            const unsigned act = __activemask();
+            const unsigned b = __ballot_sync(act, sp);
+            if (b) {
+                const int lane = threadIdx.x & 31, leader = __ffs(b) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(reinterpret_cast<unsigned long long *>(&P.ctrl->n_special),
+                                                     (unsigned long long)__popc(b));
+                base = __shfl_sync(act, base, leader);
+                if (sp) {
+                    const unsigned long long at = base + __popc(b & ((1u << lane) - 1));
+                    if ((long long)at < P.line_cap) P.special[at] = (unsigned long long)l;
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nt; i += MT_THREADS) {       // the outputs, coalesced
+            const unsigned long long o = S.pre[i];
+            P.lw[l0 + i] = (uint32_t)(o & 0xfffff);
+            P.lnm[l0 + i] = (uint32_t)((o >> 20) & 0xfffff);
+            P.lfl[l0 + i] = (uint8_t)(o >> 40);
         }
         __syncthreads();
     }
@@ -1641,12 +1686,15 @@ __global__ void k_asm_modfinal(AsmP P)
     }
 }
 
+// header words; moff[m] becomes the offset from a line's word position in
+// the line scan to its place in words[]
 __global__ void k_asm_head(AsmP P)
 {
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < P.n_mod; m += gridDim.x * blockDim.x) {
         if (P.status[m] != SPV_ASM_OK) continue;
         const AsmMod &M = P.mod[m];
         const long long at = P.word_off[m];
+        P.moff[m] = (unsigned long long)(at + 5 - (long long)P.lwo[M.first_line]);
         uint32_t h[5];
         h[0] = 0x07230203u;
         h[1] = M.hdr[0] ? (uint32_t)M.hdr[0] : 0x00010200u;
@@ -1669,7 +1717,7 @@ __global__ void k_asm_need(AsmP P)
 // workspace layout
 // ---------------------------------------------------------------------------
 struct ALayout {
-    size_t ctrl, mod, bitmap, tile_cnt, tile_off, ls, lmod, lw, lnm, lfl, lslot, lwo, occ_off, occ_slot, occ_pos, occ_first,
+    size_t ctrl, mod, bitmap, tile_cnt, tile_off, ls, lmod, lw, lnm, lfl, lslot, special, lwo, occ_off, occ_slot, occ_pos, occ_first,
         occ_rank, arena, msize, moff, sums, total;
     long long line_cap, occ_cap, arena_cap, tile_cap, bitmap_words, sums_cap;
 };
@@ -1704,6 +1752,7 @@ ALayout alayout(int32_t n_mod, uint64_t text_bytes, int64_t line_cap, int64_t na
     L.lnm = take(4 * (size_t)L.line_cap);
     L.lfl = take((size_t)L.line_cap);
     L.lslot = take(4 * (size_t)SLOT_WORDS * (size_t)L.line_cap);
+    L.special = take(8 * (size_t)L.line_cap);
     L.lwo = take(8 * (size_t)(L.line_cap + 1));
     L.occ_off = take(8 * (size_t)(L.line_cap + 1));
     L.occ_slot = take(8 * (size_t)L.occ_cap);
@@ -1780,6 +1829,7 @@ extern "C" int spv_assemble_batch(const char *text, uint64_t text_bytes, const u
     P.ls = (unsigned long long *)(w + L.ls); P.lmod = (int32_t *)(w + L.lmod);
     P.lw = (uint32_t *)(w + L.lw); P.lnm = (uint32_t *)(w + L.lnm); P.lfl = (uint8_t *)(w + L.lfl);
     P.lslot = (uint32_t *)(w + L.lslot);
+    P.special = (unsigned long long *)(w + L.special);
     P.lwo = (unsigned long long *)(w + L.lwo); P.occ_off = (unsigned long long *)(w + L.occ_off);
     P.occ_cap = L.occ_cap;
     P.occ_slot = (unsigned long long *)(w + L.occ_slot); P.occ_pos = (unsigned long long *)(w + L.occ_pos);
@@ -1834,6 +1884,7 @@ extern "C" int spv_assemble_batch(const char *text, uint64_t text_bytes, const u
     SPV_LAUNCH("k_asm_modfinal", st, k_asm_modfinal<<<gm, 256, 0, st>>>(P));
     scan(P.msize, n_mod_dev, n_mod_ll, sums, (unsigned long long *)word_off, nullptr, st);
     SPV_LAUNCH("k_asm_head", st, k_asm_head<<<gm, 256, 0, st>>>(P));
+    SPV_LAUNCH("k_asm_copy", st, k_asm_copy<<<gl, 256, 0, st>>>(P));
     SPV_LAUNCH("k_asm_emit", st, k_asm_parse<M_EMIT><<<gl, 256, 0, st>>>(P));
     SPV_LAUNCH("k_asm_need", st, k_asm_need<<<1, 1, 0, st>>>(P));
     return cudaPeekAtLastError() == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;
