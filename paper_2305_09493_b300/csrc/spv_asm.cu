@@ -1392,12 +1392,13 @@ __global__ void __launch_bounds__(256) k_asm_parse(AsmP P)
 // that a warp takes lines that walk the same code; each line's words are
 // recorded in shared memory and written to its slot as whole 32-byte
 // sectors.
-constexpr int MT_THREADS = 256, MT_LINES = 1024, MT_TEXT = 48 * 1024, MT_KEYS = 256;
+constexpr int MT_THREADS = 256, MT_LINES = 1024, MT_TEXT = 44 * 1024, MT_KEYS = 256;
 struct MTSmem {
     alignas(16) uint8_t text[MT_TEXT];
     alignas(16) uint32_t slot[MT_THREADS][SLOT_WORDS];
     unsigned long long pre[MT_LINES];    // packed prefix (0: not packed); then the packed outputs
-    int32_t mod[MT_LINES];
+    int32_t mod[MT_LINES];               // the line's module; -1: its module does not fit, or an empty line
+    uint32_t qoff[MT_LINES];             // line start - the tile's first line start
     uint16_t perm[MT_LINES];
     uint16_t len[MT_LINES];              // line length; 0xffff: longer
     uint8_t key[MT_LINES];
@@ -1406,6 +1407,7 @@ struct MTSmem {
 
 // returns the line's packed outputs: words | named << 20 | flags << 40; the
 // largest explicit id goes to max_explicit
+// (the line's module fits the line capacity and the line is not empty)
 __device__ __forceinline__ unsigned long long measure_line(const AsmP &P, long long l, int m, unsigned long long q,
                                                            const uint8_t *s, uint32_t n, const Prefix *pre,
                                                            uint32_t *sslot, uint32_t &max_explicit)
@@ -1414,22 +1416,21 @@ __device__ __forceinline__ unsigned long long measure_line(const AsmP &P, long l
     uint32_t lw = 0, lnm = 0;
     uint8_t fl = 0;
     max_explicit = 0;
-    if ((M.flags & MF_FIT_LINES) && n) {
-        const long long rel = l - M.first_line;
+    {
         if (s[0] == ';') {
             uint32_t value;
             const int f = header_line(s, n, value);
-            if (f >= 0) atomicMax(&M.hdr[f], ((unsigned long long)(rel + 1) << 32) | value);
+            if (f >= 0) atomicMax(&M.hdr[f], ((unsigned long long)(l - M.first_line + 1) << 32) | value);
         } else {
             Walk w;
             w.s = s; w.n = n; w.pos = q;
-            w.M = &M; w.text = P.text; w.mod_end = nullptr; w.rel = rel;
+            w.M = &M; w.text = P.text; w.mod_end = nullptr; w.rel = 0;
             w.arena = P.arena; w.occ_slot = P.occ_slot; w.occ_pos = P.occ_pos;
             w.max_explicit = 0; w.w64 = false; w.occ = 0; w.out = nullptr; w.out_at = 0; w.out_cap = 0;
             w.slot = sslot;
-            const uint32_t st = walk_line<M_MEASURE>(w, rel, 0u, pre);
+            const uint32_t st = walk_line<M_MEASURE>(w, 0, 0u, pre);
             if (st) {
-                atomicMin(&M.err, ((unsigned long long)rel << 8) | st);
+                atomicMin(&M.err, ((unsigned long long)(l - M.first_line) << 8) | st);
             } else {
                 fl = w.flags;
                 lw = w.words;
@@ -1485,19 +1486,23 @@ __global__ void __launch_bounds__(MT_THREADS, 3) k_asm_measure(AsmP P)
             long long qe = i + 1 < nt ? (long long)P.ls[l0 + i + 1] : e;
             if (qe > q && P.text[qe - 1] == '\n') qe--;
             const long long n = qe - q;
+            const int m = P.lmod[l0 + i];
+            const bool live = n > 0 && (P.mod[m].flags & MF_FIT_LINES);
             uint32_t key = 0;
             unsigned long long pk = 0;
-            if (n > 0 && qe <= se && S.text[q - a_al] != ';') {
+            if (!live) {
+            } else if (qe <= se && S.text[q - a_al] != ';') {
                 Prefix px;
                 const bool ok = line_prefix(S.text + (q - a_al), (uint32_t)n, px);
                 pk = pack_prefix(px, ok);
                 key = !ok || px.op < 0 ? 1u : g_spv_tables.shape[px.op];
-            } else if (n > 0 && qe > se) {
+            } else if (qe > se) {
                 key = 1;
             }
             S.len[i] = (uint16_t)(n < 0xffff ? n : 0xffff);
             S.pre[i] = pk;
-            S.mod[i] = P.lmod[l0 + i];
+            S.mod[i] = live ? m : -1;
+            S.qoff[i] = q - a < 0xffffffffll ? (uint32_t)(q - a) : 0xffffffffu;   // else read again
             S.key[i] = (uint8_t)key;
             atomicAdd(&S.hist[key], 1u);
         }
@@ -1523,14 +1528,18 @@ __global__ void __launch_bounds__(MT_THREADS, 3) k_asm_measure(AsmP P)
         for (int j = threadIdx.x; j < nt; j += MT_THREADS) {
             const int i = S.perm[j];
             const long long l = l0 + i;
-            const long long q = (long long)P.ls[l];
+            const int m = S.mod[i];
+            if (m < 0) {                                  // empty, or its module does not fit
+                S.pre[i] = 0;
+                continue;
+            }
+            const long long q = S.qoff[i] != 0xffffffffu ? a + S.qoff[i] : (long long)P.ls[l];
             long long n = S.len[i];
             if (n == 0xffff) {
                 long long qe = i + 1 < nt ? (long long)P.ls[l + 1] : e;
                 if (qe > q && P.text[qe - 1] == '\n') qe--;
                 n = qe - q;
             }
-            const int m = S.mod[i];
             uint32_t mx = 0;
             unsigned long long out = 0;
             if (n >= (1ll << 31)) {
