@@ -110,6 +110,7 @@ def measured_peaks():
 KERNEL_SOURCES = {
     "k_dis_main": ("spv_dis.cu", "spv_device.cuh", "spv_tables.cuh"),
     "k_tile": ("spv_batch.cu", "spv_device.cuh", "spv_tables.cuh"),
+    "k_asm_measure": ("spv_asm.cu", "spv_tables.cuh"),
 }
 
 
@@ -548,11 +549,28 @@ def main():
     asm_t = float(np.median(asm_ms))
     asm_kernels = {k: {"launches": v[0], "ms_per_call": v[1] / 6} for k, v in
                    sorted(aprof.items(), key=lambda kv: -kv[1][1])[:8]}
+    # the dominant kernel: reads the text and 12 bytes per line (line start,
+    # module), writes 41 bytes per line (word count, names, flags, 32-byte slot)
+    n_lines, _ = spvgpu.spv_asm_required(spvgpu._ptr(aws.buf))
+    mk_l, mk_ms = aprof["k_asm_measure"]
+    meas_ms = mk_ms / mk_l
+    meas_alg = Ltext + 53 * n_lines
+    meas_traffic, meas_inst = None, None
+    if os.path.exists(tj):
+        kt = json.load(open(tj)).get("kernels", {}).get("k_asm_measure", {})
+        if kt.get("source_sha") == source_hash("k_asm_measure") and kt.get("lines") == n_lines:
+            meas_traffic, meas_inst = kt.get("bytes_per_launch"), kt.get("warp_instructions_per_launch")
     asm_leg = {"scope": "the step's disassembly text back to words (named ids, types, constants, headers)",
                "ms": asm_t, "text_gbs": Ltext / (asm_t * 1e-3) / 1e9,
                "achieved_gbs": (Ltext + 4 * W) / (asm_t * 1e-3) / 1e9,
                "round_trip_exact": bool(torch.equal(a_words, words)) and bool(torch.equal(a_off, mod_off))
                and bool((a_st == 0).all().item()),
+               "lines": n_lines,
+               "roofline": {"bound": "hbm", "kernel": "k_asm_measure",
+                            "achieved": meas_alg / (meas_ms * 1e-3) / 1e9, "peak": peak, "peak_kind": peak_kind,
+                            "unit": "GB/s", "frac": meas_alg / (meas_ms * 1e-3) / 1e9 / peak,
+                            "traffic": meas_traffic, "algorithmic_bytes_per_launch": meas_alg,
+                            "ms_per_launch": meas_ms, "issue": issue_roofline(meas_inst, meas_ms, clk)},
                "kernels": asm_kernels}
 
     # batched vs per-module launches (decode+validate+encode, same exact output)

@@ -96,7 +96,8 @@ def _hand_texts():
              'OpEntryPoint Kernel %main "k"\n%void = OpTypeVoid\n%fn = OpTypeFunction %void\n'
              "%main = OpFunction %void None %fn\n%entry = OpLabel\nOpReturn\nOpFunctionEnd\n")
     t.append("%7 = OpTypeVoid\n%a_7 = OpTypeVoid\n%_7 = OpTypeVoid\n%a7 = OpTypeVoid\n%_ = OpTypeVoid\n"
-             "%7a = OpTypeVoid\n%a7 = OpTypeVoid\n")
+             "%7a = OpTypeVoid\n%a7 = OpTypeVoid\n%%5 = OpTypeVoid\n%a%_5 = OpTypeVoid\n%00012 = OpTypeVoid\n"
+             "%_4294967296 = OpTypeVoid\n")
     t.append(HEAD + r'OpExtension "a\"b\\c\x41\x4a\xg1\q"' + "\nOpName %3 \"\"\nOpName %3 \"abcd\"\n")
     t.append("; Version: 1.5\n; Generator: 0xDEADbeef\n; Bound: 99\n; Schema: 3\nOpNop\n")
     t.append("; Version: 1.5 \n; Version:1.3\n; Bound: 4294967296\n; Bound: 9x\n; bound: 5\nOpNop\n")

@@ -69,6 +69,14 @@ def test_named_ids_by_first_appearance():
     assert words_of(text2) == list(H.module(body2, bound=12, generator=0))
 
 
+def test_more_id_forms():
+    # %%5 is a name (the digits follow a '%' that is not the first byte);
+    # %a%_5 is id 5; %00012 is id 12
+    w = words_of("%%5 = OpTypeVoid\n%a%_5 = OpTypeVoid\n%00012 = OpTypeVoid\n")
+    assert w[5:] == [H.ins(H.OpTypeVoid, i)[k] for i in (13, 5, 12) for k in (0, 1)]
+    assert asm("%_4294967296 = OpTypeVoid\n") == (None, 1)
+
+
 def test_explicit_id_forms():
     # %7, %a_7 and %_7 are all id 7; %a7, %_ and %7a are names
     w = words_of("%7 = OpTypeVoid\n%a_7 = OpTypeVoid\n%_7 = OpTypeVoid\n%a7 = OpTypeVoid\n%_ = OpTypeVoid\n"
