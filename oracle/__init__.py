@@ -58,6 +58,9 @@ def _L():
         lib.orc_disassemble.restype = ctypes.c_int64
         lib.orc_disassemble.argtypes = [P, P, ctypes.c_int32, ctypes.c_int, ctypes.c_int, P,
                                         ctypes.c_int64, P]
+        lib.orc_build.restype = ctypes.c_int64
+        lib.orc_build.argtypes = [P, P, P, P, P, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, P,
+                                  ctypes.c_int64, P, P, P, P]
         lib.orc_assemble.restype = ctypes.c_int64
         lib.orc_assemble.argtypes = [ctypes.c_char_p, ctypes.c_int64, P, ctypes.c_int64]
         lib.orc_op_info.restype = ctypes.c_int
@@ -213,6 +216,32 @@ def assemble_batch(text: bytes, text_off):
         word_off[m + 1] = word_off[m] + len(w)
     words = np.concatenate(parts) if parts else np.zeros(0, np.uint32)
     return words.astype(np.uint32), word_off, status, err
+
+
+# Builder module status codes.
+BUILD_STATUS = ["OK", "BAD_REF", "BAD_ROW"]
+
+
+def build_batch(ol, version: int = 0x00010200, generator: int = 0):
+    """Modules from op lists (a dict with op, opd_off, opd, opd_ref, row_off).
+    Returns (words, word_off, status, err_row, ids): ids[r] is the id given to
+    row r (0 if its opcode has no result id)."""
+    op = np.ascontiguousarray(ol["op"], np.uint16)
+    opd_off = np.ascontiguousarray(ol["opd_off"], np.int64)
+    opd = np.ascontiguousarray(ol["opd"], np.uint32)
+    opd_ref = np.ascontiguousarray(ol["opd_ref"], np.uint8)
+    row_off = np.ascontiguousarray(ol["row_off"], np.int64)
+    m = len(row_off) - 1
+    word_off = np.zeros(m + 1, np.int64)
+    status = np.zeros(max(1, m), np.uint32)
+    err = np.zeros(max(1, m), np.int64)
+    ids = np.zeros(max(1, len(op)), np.uint32)
+    n = _L().orc_build(_p(op), _p(opd_off), _p(opd), _p(opd_ref), _p(row_off), m, version, generator, None, 0,
+                       _p(word_off), _p(status), _p(err), _p(ids))
+    out = np.zeros(max(1, n), np.uint32)
+    _L().orc_build(_p(op), _p(opd_off), _p(opd), _p(opd_ref), _p(row_off), m, version, generator, _p(out), n,
+                   _p(word_off), _p(status), _p(err), _p(ids))
+    return out[:n], word_off, status[:m], err[:m], ids[:len(op)]
 
 
 def op_info(op: int):

@@ -1566,6 +1566,79 @@ int64_t orc_assemble(const char *text, int64_t len, uint32_t *out, int64_t cap)
 }
 
 /* ------------------------------------------------------------------ */
+/* Build modules from op lists, section 3.4.2 ("Enabling Function      */
+/* Composition"): instructions are added in order and every one that   */
+/* has a result takes a new id from the module, which alone hands ids  */
+/* out (getNextId). Here a module is a list of rows: an opcode and its */
+/* operands without the result id; an operand is a literal word or a   */
+/* reference to another row of the module (its result id). The ids are */
+/* handed out in row order: 1, 2, ... to the rows whose opcode has a   */
+/* result id. For an opcode with a result type, the first operand is   */
+/* the result type and the result id follows it. Checks, first bad row */
+/* of the module, in this order within a row: an opcode with a result  */
+/* type but no operand, or an instruction over 65535 words (BAD_ROW);  */
+/* a reference outside the module or to a row without a result id      */
+/* (BAD_REF). A module with a bad row has no words.                    */
+/* ------------------------------------------------------------------ */
+enum { BUILD_OK = 0, BUILD_BAD_REF = 1, BUILD_BAD_ROW = 2 };
+
+int64_t orc_build(const uint16_t *op, const int64_t *opd_off, const uint32_t *opd, const uint8_t *opd_ref,
+                  const int64_t *row_off, int32_t n_mod, uint32_t version, uint32_t generator,
+                  uint32_t *out, int64_t cap, int64_t *word_off, uint32_t *status, int64_t *err_row, uint32_t *ids)
+{
+    int64_t n = 0;
+    for (int32_t m = 0; m < n_mod; m++) {
+        const int64_t r0 = row_off[m], r1 = row_off[m + 1];
+        word_off[m] = n;
+        /* getNextId, once per row with a result, in row order */
+        uint32_t next = 1;
+        for (int64_t r = r0; r < r1; r++) {
+            const OpInfo *oi = find_op(op[r]);
+            ids[r] = (oi && oi->rid) ? next++ : 0;
+        }
+        /* checks */
+        uint32_t st = BUILD_OK;
+        int64_t bad = -1;
+        for (int64_t r = r0; r < r1 && st == BUILD_OK; r++) {
+            const OpInfo *oi = find_op(op[r]);
+            const int64_t nopd = opd_off[r + 1] - opd_off[r];
+            if ((oi && oi->rtype && nopd == 0) || 1 + nopd + ((oi && oi->rid) ? 1 : 0) > 65535) {
+                st = BUILD_BAD_ROW; bad = r - r0; break;
+            }
+            for (int64_t k = opd_off[r]; k < opd_off[r + 1]; k++) {
+                if (!opd_ref[k]) continue;
+                if ((int64_t)opd[k] >= r1 - r0 || ids[r0 + opd[k]] == 0) { st = BUILD_BAD_REF; bad = r - r0; break; }
+            }
+        }
+        status[m] = st;
+        err_row[m] = bad;
+        if (st != BUILD_OK) continue;
+        /* the words: header, then each row */
+        const uint32_t head[5] = {ORC_MAGIC, version, generator, next, 0};
+        for (int i = 0; i < 5; i++) { if (n < cap) out[n] = head[i]; n++; }
+        for (int64_t r = r0; r < r1; r++) {
+            const OpInfo *oi = find_op(op[r]);
+            const int rt = oi && oi->rtype, rid = oi && oi->rid;
+            const int64_t nopd = opd_off[r + 1] - opd_off[r];
+            const uint32_t wc = (uint32_t)(1 + nopd + (rid ? 1 : 0));
+            if (n < cap) out[n] = (wc << 16) | op[r];
+            n++;
+            for (int64_t j = 0; j <= nopd; j++) {
+                /* the result id goes after the result type, or first */
+                if (rid && j == (rt ? 1 : 0)) { if (n < cap) out[n] = ids[r]; n++; }
+                if (j == nopd) break;
+                const int64_t k = opd_off[r] + j;
+                const uint32_t v = opd_ref[k] ? ids[r0 + opd[k]] : opd[k];
+                if (n < cap) out[n] = v;
+                n++;
+            }
+        }
+    }
+    word_off[n_mod] = n;
+    return n;
+}
+
+/* ------------------------------------------------------------------ */
 /* Table queries (for the test that cross-checks the two tables).      */
 /* ------------------------------------------------------------------ */
 int orc_op_info(uint32_t opn, int *has_rtype, int *has_rid, int *cap, const char **name)

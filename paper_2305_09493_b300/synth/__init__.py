@@ -52,6 +52,9 @@ def _L():
         lib.synth_batch_shape.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
                                           ctypes.c_int32, P, P]
+        lib.synth_oplist_batch.restype = ctypes.c_int64
+        lib.synth_oplist_batch.argtypes = [ctypes.c_int32, ctypes.c_uint64, P, P, ctypes.c_int32] + [P] * 8 + \
+            [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         lib.synth_batch.restype = ctypes.c_int64
         lib.synth_batch.argtypes = [ctypes.c_int32, ctypes.c_uint64, P, P, ctypes.c_int32, P,
                                     ctypes.c_int64, P]
@@ -131,3 +134,31 @@ def size_bins(per_bin: int = 1000, bins=(200, 2000, 20_000, 50_000), seed0: int 
         w, off = batch(n_instr, n_kernels, seed0 + 1_000_000 * (b + 1))
         out.append((size, w, off))
     return out
+
+
+def oplist_batch(n_instr, n_kernels, seed0: int = 0, string_permille: int = 0):
+    """The batch of batch() as op lists, what a JIT backend hands a builder:
+    one row per instruction, its operands without the result id, id operands
+    as references to the defining row of the module. Returns a dict: words,
+    mod_off (the batch itself), is_id (1 for its id words), op, opd_off, opd,
+    opd_ref, row_off."""
+    n_instr = np.ascontiguousarray(n_instr, np.int64)
+    n_kernels = np.ascontiguousarray(n_kernels, np.int32)
+    m = len(n_instr)
+    lib = _L()
+    nr, no = ctypes.c_int64(0), ctypes.c_int64(0)
+    total = lib.synth_oplist_batch(m, seed0, _p(n_instr), _p(n_kernels), string_permille, *([None] * 8),
+                                   ctypes.byref(nr), ctypes.byref(no))
+    d = {"words": np.zeros(total, np.uint32), "mod_off": np.zeros(m + 1, np.int64),
+         "is_id": np.zeros(total, np.uint8), "op": np.zeros(nr.value, np.uint16),
+         "opd_off": np.zeros(nr.value + 1, np.int64), "opd": np.zeros(no.value, np.uint32),
+         "opd_ref": np.zeros(no.value, np.uint8), "row_off": np.zeros(m + 1, np.int64)}
+    lib.synth_oplist_batch(m, seed0, _p(n_instr), _p(n_kernels), string_permille, _p(d["words"]), _p(d["mod_off"]),
+                           _p(d["is_id"]), _p(d["op"]), _p(d["opd_off"]), _p(d["opd"]), _p(d["opd_ref"]),
+                           _p(d["row_off"]), ctypes.byref(nr), ctypes.byref(no))
+    return d
+
+
+def oplist_module_batch(n_mod: int = 10_000, seed0: int = 0, median: float = 1500.0):
+    n_instr, n_kernels = batch_shape(n_mod, seed0, median)
+    return oplist_batch(n_instr, n_kernels, seed0)

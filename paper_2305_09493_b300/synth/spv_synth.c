@@ -130,6 +130,10 @@ typedef struct {
 
 static uint32_t new_id(Gen *g) { uint32_t id = g->next_id++; pool_add(&g->all_ids, id); return id; }
 
+/* first id handed out (1 normally); synth_oplist_batch generates each module
+ * a second time from a high base to tell id words from literal words */
+static uint32_t s_id_base = 1;
+
 static void random_ascii(Rng *r, char *buf, int len)
 {
     for (int i = 0; i < len; i++) buf[i] = (char)(0x20 + rng_below(r, 0x7f - 0x20));
@@ -341,7 +345,7 @@ int64_t synth_module(uint64_t seed, int64_t func_instr, int32_t n_kernels, int32
     Gen *g = (Gen *)calloc(1, sizeof(Gen));
     rng_seed(&g->rng, seed);
     Rng *r = &g->rng;
-    g->next_id = 1;
+    g->next_id = s_id_base;
     if (n_kernels < 1) n_kernels = 1;
     if (n_funcs < n_kernels) n_funcs = n_kernels;
 
@@ -504,5 +508,92 @@ int64_t synth_batch(int32_t n_mod, uint64_t seed0, const int64_t *n_instr, const
         total += n;
     }
     mod_off[n_mod] = total;
+    return total;
+}
+
+/* ---------------- op lists: the same modules as a JIT backend's rows ----------------
+ * Each instruction of a batch becomes one row: its opcode and its operands,
+ * the result id left out; an operand that is an id becomes a reference to
+ * the row (within the module) whose result it is. The generator knows which
+ * words are ids by generating every module twice, with ids from 1 and from
+ * 2^30: exactly the id words differ. The result id's place is word 2 for the
+ * opcodes below that have a result type, word 1 for the others with a result
+ * id (the generator's own opcodes only). */
+static int res_pos(uint32_t op)
+{
+    switch (op) {
+    case O_String: case O_ExtInstImport: case O_TypeVoid: case O_TypeBool: case O_TypeInt: case O_TypeFloat:
+    case O_TypeVector: case O_TypePointer: case O_TypeFunction: case O_Label:
+        return 1;
+    case O_Source: case O_Name: case O_MemoryModel: case O_EntryPoint: case O_ExecutionMode: case O_Capability:
+    case O_FunctionEnd: case O_Store: case O_Decorate: case O_ControlBarrier: case O_LoopMerge:
+    case O_SelectionMerge: case O_Branch: case O_BranchConditional: case O_Return:
+        return 0;
+    default:
+        return 2;
+    }
+}
+
+/* Generates the batch of synth_batch (same arguments, same words and
+ * mod_off) and its op list: op[r], opd_off[r..r+1) into opd / opd_ref,
+ * row_off[m..m+1] the rows of module m, is_id[w] = 1 for id words (header
+ * words excluded). Outputs may be NULL to size: *n_rows and *n_opd are set
+ * either way. Returns the total words. */
+int64_t synth_oplist_batch(int32_t n_mod, uint64_t seed0, const int64_t *n_instr, const int32_t *n_kernels,
+                           int32_t string_permille, uint32_t *out, int64_t *mod_off, uint8_t *is_id,
+                           uint16_t *op, int64_t *opd_off, uint32_t *opd, uint8_t *opd_ref, int64_t *row_off,
+                           int64_t *n_rows, int64_t *n_opd)
+{
+    int64_t total = 0, rows = 0, nopd = 0;
+    for (int32_t m = 0; m < n_mod; m++) {
+        int32_t nk = n_kernels[m];
+        int64_t module_level = 3 + 2 + 3 * nk + 1 + 20 + 24;
+        int64_t fi = n_instr[m] - module_level;
+        if (fi < 12 * nk) fi = 12 * nk;
+        int64_t ni; uint32_t b;
+        s_id_base = 1;
+        int64_t n = synth_module(seed0 + (uint64_t)m, fi, nk, nk, 40, 20, 10, string_permille, NULL, 0, NULL, 0, &ni, &b);
+        uint32_t *w1 = (uint32_t *)malloc((size_t)n * 4), *w2 = (uint32_t *)malloc((size_t)n * 4);
+        int64_t *st = (int64_t *)malloc((size_t)ni * 8);
+        synth_module(seed0 + (uint64_t)m, fi, nk, nk, 40, 20, 10, string_permille, w1, n, st, ni, &ni, &b);
+        s_id_base = 1u << 30;
+        int64_t ni2; uint32_t b2;
+        synth_module(seed0 + (uint64_t)m, fi, nk, nk, 40, 20, 10, string_permille, w2, n, NULL, 0, &ni2, &b2);
+        s_id_base = 1;
+        /* the row that defines each id */
+        int64_t *def = (int64_t *)malloc((size_t)b * 8);
+        for (uint32_t k = 0; k < b; k++) def[k] = -1;
+        for (int64_t i = 0; i < ni; i++) {
+            int p = res_pos(w1[st[i]] & 0xffffu);
+            if (p) def[w1[st[i] + p]] = i;
+        }
+        if (mod_off) mod_off[m] = total;
+        if (row_off) row_off[m] = rows;
+        for (int64_t k = 0; k < n; k++) {
+            if (out) out[total + k] = w1[k];
+            if (is_id) is_id[total + k] = (uint8_t)(k >= 5 && w1[k] != w2[k]);
+        }
+        for (int64_t i = 0; i < ni; i++) {
+            int64_t a = st[i], e = i + 1 < ni ? st[i + 1] : n;
+            int p = res_pos(w1[a] & 0xffffu);
+            if (op) op[rows] = (uint16_t)(w1[a] & 0xffffu);
+            if (opd_off) opd_off[rows] = nopd;
+            for (int64_t k = a + 1; k < e; k++) {
+                if (p && k == a + p) continue;
+                int ref = w1[k] != w2[k];
+                if (opd) opd[nopd] = ref ? (uint32_t)def[w1[k]] : w1[k];
+                if (opd_ref) opd_ref[nopd] = (uint8_t)ref;
+                nopd++;
+            }
+            rows++;
+        }
+        total += n;
+        free(w1); free(w2); free(st); free(def);
+    }
+    if (mod_off) mod_off[n_mod] = total;
+    if (row_off) row_off[n_mod] = rows;
+    if (opd_off) opd_off[rows] = nopd;
+    *n_rows = rows;
+    *n_opd = nopd;
     return total;
 }
