@@ -372,6 +372,57 @@ int spv_assemble_batch(const char *text, uint64_t text_bytes, const uint64_t *te
 int spv_asm_required(const void *workspace, int64_t *lines, int64_t *names);
 
 /*
+ * Builder: modules from op lists (section 3.4.2, "Enabling Function
+ * Composition"), for a whole batch at once. In the paper each instruction
+ * is added to its scope in order and each one with a result first asks the
+ * module for the next id (getNextId). Here a module is a list of rows: row r
+ * is an opcode op[r] and its operands opd[opd_off[r] .. opd_off[r+1]), the
+ * result id left out; operand k is a literal word (opd_ref[k] = 0) or a
+ * reference to row opd[k] of the same module, counted from the module's
+ * first row (opd_ref[k] = 1), which stands for that row's result id. The
+ * rows whose opcode has a result id (by the opcode table) get the ids 1, 2,
+ * ... of their module in row order; the result id is written after the
+ * result type (the first operand) when the opcode has one, else first.
+ * Opcodes outside the table have no result id; their operands are copied.
+ * Checks, the first bad row of a module winning (in a row: the first two
+ * before the references, in operand order): an opcode with a result type
+ * and no operand, or an instruction over 65535 words, is SPV_BUILD_BAD_ROW;
+ * a reference outside the module or to a row without a result id is
+ * SPV_BUILD_BAD_REF. A module that is not SPV_BUILD_OK has no words.
+ * Module m's words: magic, version, generator, bound (its ids + 1), schema
+ * 0, then its rows' instructions; they go to words[word_off[m] ..
+ * word_off[m+1]) (word_off: device, n_modules + 1 entries, always filled);
+ * no word at or past words_capacity is written. ids (device, n_rows, may be
+ * NULL) gets each row's id, 0 for rows without one. status (device,
+ * n_modules) gets spv_build_status codes, err_row (device, may be NULL) the
+ * module-relative first bad row, else -1. All arrays are device memory.
+ * row_off and opd_off must not decrease, row_off[n_modules] <= n_rows;
+ * otherwise every module is SPV_BUILD_BAD_OFFSETS.
+ */
+typedef struct spv_oplist {
+    const uint16_t *op;         /* [n_rows] */
+    const int64_t *opd_off;     /* [n_rows + 1] */
+    const uint32_t *opd;        /* [opd_off[n_rows]] operand values */
+    const uint8_t *opd_ref;     /* [opd_off[n_rows]] 1: opd is a row index within the module */
+    const int64_t *row_off;     /* [n_modules + 1] module m is rows row_off[m] .. row_off[m+1] */
+    int32_t n_modules;
+    int64_t n_rows;
+} spv_oplist;
+
+typedef enum spv_build_status {
+    SPV_BUILD_OK = 0,
+    SPV_BUILD_BAD_REF = 1,
+    SPV_BUILD_BAD_ROW = 2,
+    SPV_BUILD_BAD_OFFSETS = 3
+} spv_build_status;
+
+size_t spv_build_workspace_bytes(int32_t n_modules, int64_t n_rows);
+
+int spv_build_batch(const spv_oplist *ol, uint32_t version, uint32_t generator, uint32_t *words,
+                    int64_t words_capacity, int64_t *word_off, uint32_t *ids, uint32_t *status, int64_t *err_row,
+                    void *workspace, size_t workspace_bytes, spv_stream_t stream);
+
+/*
  * Serving: continuous batching of modules that arrive one by one, as a JIT
  * backend produces them (the paper's use case, section 4). A server owns a
  * device pool and a pinned host pool. Submitted modules wait in a queue; a

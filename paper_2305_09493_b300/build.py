@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspvgpu.so")
-SOURCES = ["spv_asm.cu", "spv_batch.cu", "spv_dis.cu", "spv_info.cu", "spv_layout.cu", "spv_pipe.cu", "spv_prof.cu", "spv_serve.cu"]
+SOURCES = ["spv_asm.cu", "spv_batch.cu", "spv_build.cu", "spv_dis.cu", "spv_info.cu", "spv_layout.cu", "spv_pipe.cu", "spv_prof.cu", "spv_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

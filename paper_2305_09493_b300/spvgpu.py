@@ -46,6 +46,12 @@ class SpvConfig(ctypes.Structure):
                 ("per_module", ctypes.c_int32), ("max_spins", ctypes.c_int64), ("test_stall_tile", ctypes.c_int64)]
 
 
+class SpvOplist(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_void_p), ("opd_off", ctypes.c_void_p), ("opd", ctypes.c_void_p),
+                ("opd_ref", ctypes.c_void_p), ("row_off", ctypes.c_void_p), ("n_modules", ctypes.c_int32),
+                ("n_rows", ctypes.c_int64)]
+
+
 class SpvDisOpts(ctypes.Structure):
     _fields_ = [("inline_names", ctypes.c_int32), ("header", ctypes.c_int32), ("max_spins", ctypes.c_int64),
                 ("test_stall_tile", ctypes.c_int64)]
@@ -101,6 +107,11 @@ def load():
     lib.spv_asm_workspace_bytes.argtypes = [i32, ctypes.c_uint64, i64, i64]
     lib.spv_assemble_batch.restype = ctypes.c_int
     lib.spv_assemble_batch.argtypes = [P, ctypes.c_uint64, P, i32, P, i64, P, P, P, P, sz, i64, i64, P]
+    lib.spv_build_workspace_bytes.restype = sz
+    lib.spv_build_workspace_bytes.argtypes = [i32, i64]
+    lib.spv_build_batch.restype = ctypes.c_int
+    lib.spv_build_batch.argtypes = [ctypes.POINTER(SpvOplist), ctypes.c_uint32, ctypes.c_uint32, P, i64, P, P, P, P,
+                                    P, sz, P]
     lib.spv_asm_required.restype = ctypes.c_int
     lib.spv_asm_required.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     _lib = lib
@@ -456,6 +467,60 @@ def assemble(text, text_off, *, words=None, workspace=None, stream=None, line_ca
             return words[:total], word_off, status[:m], err[:m]
         words = torch.empty(total, dtype=torch.int32, device=dev)
     raise SpvError("assembler buffer sizing failed")
+
+
+# ---------------------------------------------------------------------------
+# builder
+# ---------------------------------------------------------------------------
+BUILD_STATUS = ["OK", "BAD_REF", "BAD_ROW", "BAD_OFFSETS"]
+
+
+def spv_build_workspace_bytes(n_modules, n_rows):
+    return load().spv_build_workspace_bytes(n_modules, n_rows)
+
+
+def spv_build_batch(ol, version, generator, words, words_capacity, word_off, ids, status, err_row, workspace,
+                    ws_bytes, stream):
+    return load().spv_build_batch(ctypes.byref(ol), version, generator, words, words_capacity, word_off, ids,
+                                  status, err_row, workspace, ws_bytes, stream)
+
+
+class BuildWorkspace:
+    def __init__(self, n_modules, n_rows, device):
+        self.bytes = spv_build_workspace_bytes(n_modules, n_rows)
+        self.buf = torch.empty(max(1, self.bytes), dtype=torch.uint8, device=device)
+
+
+def build_modules(op, opd_off, opd, opd_ref, row_off, *, version=0x00010200, generator=0, words=None,
+                  workspace=None, stream=None, sync=True, want_ids=True):
+    """Modules from op lists (device tensors: op int16 (the uint16 opcodes),
+    opd_off int64, opd int32 (the uint32 operand values), opd_ref uint8,
+    row_off int64). With sync (default) the call waits, grows the word buffer
+    if needed and returns (words int32 trimmed, word_off int64, status int32,
+    err_row int64, ids int32 or None)."""
+    m = row_off.numel() - 1
+    n_rows = op.numel()
+    dev = row_off.device
+    if workspace is None:
+        workspace = BuildWorkspace(m, n_rows, dev)
+    if words is None:
+        words = torch.empty(max(16, opd.numel() + 2 * n_rows + 5 * m), dtype=torch.int32, device=dev)
+    word_off = torch.empty(m + 1, dtype=torch.int64, device=dev)
+    status = torch.empty(max(1, m), dtype=torch.int32, device=dev)
+    err = torch.empty(max(1, m), dtype=torch.int64, device=dev)
+    ids = torch.empty(max(1, n_rows), dtype=torch.int32, device=dev) if want_ids else None
+    ol = SpvOplist(_ptr(op), _ptr(opd_off), _ptr(opd), _ptr(opd_ref), _ptr(row_off), m, n_rows)
+    for _ in range(2):
+        rc = spv_build_batch(ol, version, generator, _ptr(words), words.numel(), _ptr(word_off), _ptr(ids),
+                             _ptr(status), _ptr(err), _ptr(workspace.buf), workspace.bytes, _stream(stream))
+        _check(rc, "spv_build_batch")
+        if not sync:
+            return words, word_off, status[:m], err[:m], (ids[:n_rows] if ids is not None else None)
+        total = int(word_off[-1].item())
+        if total <= words.numel():
+            return words[:total], word_off, status[:m], err[:m], (ids[:n_rows] if ids is not None else None)
+        words = torch.empty(total, dtype=torch.int32, device=dev)
+    raise SpvError("builder buffer sizing failed")
 
 
 # ---------------------------------------------------------------------------
