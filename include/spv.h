@@ -542,6 +542,17 @@ void spv_pipe_destroy(spv_pipe *p);
 /* Host-side queries of the library's own opcode / enumerant tables (no GPU
  * needed). spv_op_info returns 0 and fills the outputs for a known opcode,
  * -1 otherwise; cap is the capability the opcode requires or -1. */
+/* Sizes of a batch's outputs (a convenience for sizing buffers):
+ * *rows_upper (may be NULL) = n_words - 5 * n_modules, at least 0, an upper
+ * bound of the decoded rows from the batch's shape alone (an instruction
+ * holds at least one word, a header five). *text_bytes (may be NULL) = the
+ * exact size of spv_disassemble_batch's text with these options, found by
+ * decoding and measuring the batch on the stream with scratch the call
+ * allocates (cudaMallocAsync) and frees; with text_bytes the call is
+ * synchronous. Returns SPV_SUCCESS or an SPV_E_* code. */
+int spv_query_sizes(const spv_batch *batch, const spv_dis_opts *opts, int64_t *rows_upper, uint64_t *text_bytes,
+                    spv_stream_t stream);
+
 int spv_op_info(uint32_t opcode, int *has_rtype, int *has_rid, int *cap, const char **name);
 /* kind is one of the enumeration names used by the operand lists
  * ("Capability", "Decoration", ...). Returns 0 for a known enumerant. */

@@ -1,5 +1,7 @@
 // spv_info.cu -- host-side queries of the compiled opcode / enumerant tables
-// (the same compile-time tables the kernels read).
+// (the same compile-time tables the kernels read), and the sizes of a
+// batch's outputs.
+#include <cuda_runtime.h>
 #include <string.h>
 #include "../../include/spv.h"
 #include "spv_tables.cuh"
@@ -59,3 +61,56 @@ extern "C" int spv_enum_info(const char *kind, uint32_t value, const char **name
 }
 
 extern "C" const char *spv_version(void) { return "spvgpu 0.1 (sm_103a)"; }
+
+// Sizes of a batch's outputs: rows_upper from the shape alone; text_bytes
+// exactly, by a decode and a disassembly with no text buffer (the measuring
+// half of spv_disassemble_batch) on the stream, with scratch allocated and
+// freed here; the call waits for the stream.
+extern "C" int spv_query_sizes(const spv_batch *batch, const spv_dis_opts *opts, int64_t *rows_upper,
+                               uint64_t *text_bytes, spv_stream_t stream)
+{
+    if (!batch || batch->n_modules < 0 || batch->n_words < 0) return SPV_E_ARG;
+    const int64_t M = batch->n_modules, W = batch->n_words;
+    if (rows_upper) *rows_upper = W > 5 * M ? W - 5 * M : 0;
+    if (!text_bytes) return SPV_SUCCESS;
+    *text_bytes = 0;
+    if (M == 0) return SPV_SUCCESS;
+    if (!batch->words || !batch->mod_off) return SPV_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t R = W > 0 ? W : 1;
+    const size_t ws = spv_workspace_bytes((int32_t)M, W, 0, nullptr);
+    const size_t dws = spv_dis_workspace_bytes((int32_t)M, W, R, 0);
+    const size_t table_bytes = (size_t)R * (2 + 2 + 8 + 4 + 4 + 4) + (size_t)(M + 1) * 8 + (size_t)M * 4;
+    const size_t per_mod = (size_t)M * (4 + 8 + 4) + (size_t)(M + 1) * 8;
+    const size_t total = ws + dws + table_bytes + per_mod + 64 * 16;
+    char *buf = nullptr;
+    if (cudaMallocAsync((void **)&buf, total, st) != cudaSuccess) return SPV_E_CUDA;
+    size_t o = 0;
+    auto take = [&](size_t n) { char *p = buf + o; o += (n + 255) & ~(size_t)255; return p; };
+    spv_table t{};
+    t.op = (uint16_t *)take((size_t)R * 2);
+    t.wc = (uint16_t *)take((size_t)R * 2);
+    t.off = (uint64_t *)take((size_t)R * 8);
+    t.rtype = (uint32_t *)take((size_t)R * 4);
+    t.rid = (uint32_t *)take((size_t)R * 4);
+    t.mod = (uint32_t *)take((size_t)R * 4);
+    t.mod_first_row = (int64_t *)take((size_t)(M + 1) * 8);
+    t.mod_n_instr = (uint32_t *)take((size_t)M * 4);
+    t.capacity_rows = R;
+    uint32_t *status = (uint32_t *)take((size_t)M * 4);
+    int64_t *err = (int64_t *)take((size_t)M * 8);
+    uint32_t *dst = (uint32_t *)take((size_t)M * 4);
+    uint64_t *toff = (uint64_t *)take((size_t)(M + 1) * 8);
+    void *w1 = take(ws), *w2 = take(dws);
+    int rc = spv_decode_batch(batch, &t, status, err, w1, ws, nullptr, stream);
+    if (rc == SPV_SUCCESS)
+        rc = spv_disassemble_batch(batch, &t, opts, nullptr, 0, toff, dst, w2, dws, 0, stream);
+    uint64_t total_text = 0;
+    if (rc == SPV_SUCCESS &&
+        cudaMemcpyAsync(&total_text, toff + M, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = SPV_E_CUDA;
+    cudaFreeAsync(buf, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == SPV_SUCCESS) rc = SPV_E_CUDA;
+    if (rc == SPV_SUCCESS) *text_bytes = total_text;
+    return rc;
+}

@@ -112,6 +112,8 @@ def load():
     lib.spv_build_batch.restype = ctypes.c_int
     lib.spv_build_batch.argtypes = [ctypes.POINTER(SpvOplist), ctypes.c_uint32, ctypes.c_uint32, P, i64, P, P, P, P,
                                     P, sz, P]
+    lib.spv_query_sizes.restype = ctypes.c_int
+    lib.spv_query_sizes.argtypes = [BP, DOP, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_uint64), P]
     lib.spv_asm_required.restype = ctypes.c_int
     lib.spv_asm_required.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     _lib = lib
@@ -367,6 +369,17 @@ def encode(words, mod_off, table, *, recompute_bound=True, out=None, stream=None
                           _stream(stream))
     _check(rc, "spv_encode_batch")
     return out
+
+
+def query_sizes(words, mod_off, *, inline_names=True, header=True, stream=None):
+    """(rows_upper, text_bytes) of a batch: a shape bound on the decoded rows
+    and the exact text size of disassemble() with these options (waits)."""
+    rows, text = ctypes.c_int64(0), ctypes.c_uint64(0)
+    opts = SpvDisOpts(1 if inline_names else 0, 1 if header else 0, 0, 0)
+    rc = load().spv_query_sizes(ctypes.byref(batch_of(words, mod_off)), ctypes.byref(opts), ctypes.byref(rows),
+                                ctypes.byref(text), _stream(stream))
+    _check(rc, "spv_query_sizes")
+    return int(rows.value), int(text.value)
 
 
 class DisWorkspace:
