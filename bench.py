@@ -551,12 +551,14 @@ def main():
     # logical layout and scopes over the decoded table (spv_layout_batch):
     # reads the op column (2 bytes per row) and the module row offsets
     lay_ms = []
+    lws = torch.empty(max(1, spvgpu.load().spv_layout_workspace_bytes(M, table.capacity_rows)), dtype=torch.uint8,
+                      device=dev)
     for k in range(6):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if flush is not None:
             flush.zero_()
         a.record(stream)
-        lst, _ = spvgpu.layout(table, M)
+        lst, _ = spvgpu.layout(table, M, workspace=lws)
         b.record(stream)
         torch.cuda.synchronize()
         if k:

@@ -211,7 +211,10 @@ int spv_autotune_batch(const spv_batch *batch, spv_table *table, uint32_t *statu
  * mod_first_row[m + 1] - 1, capped at capacity_rows). Writes
  * layout_status[n_modules] (spv_layout_status) and layout_err_row: the
  * module-local row of the first error in row order (the row count for
- * SPV_LAYOUT_UNCLOSED), -1 when OK. No workspace; asynchronous on stream.
+ * SPV_LAYOUT_UNCLOSED), -1 when OK. Asynchronous on stream. workspace:
+ * device scratch of at least spv_layout_workspace_bytes(n_modules,
+ * table->capacity_rows) bytes (modules of more than 16,384 rows are split
+ * into segments whose summaries it holds).
  */
 enum spv_layout_status {
     SPV_LAYOUT_OK = 0,
@@ -222,8 +225,9 @@ enum spv_layout_status {
                                           open block; a parameter after a label; OpFunctionEnd in an open block */
     SPV_LAYOUT_UNCLOSED = 5            /* the rows end inside a function */
 };
+size_t spv_layout_workspace_bytes(int32_t n_modules, int64_t capacity_rows);
 int spv_layout_batch(const spv_table *table, int32_t n_modules, uint32_t *layout_status, int64_t *layout_err_row,
-                     spv_stream_t stream);
+                     void *workspace, size_t workspace_bytes, spv_stream_t stream);
 /* Layout class of an opcode in the library's table (host query):
  * 0 neutral, 1 module section, 2 OpUndef / OpVariable (section 9 at module
  * scope, body in a block), 3 OpFunction (section 10), 4 OpFunctionParameter,

@@ -97,7 +97,9 @@ def load():
     lib.spv_process_batch_noalloc.restype = ctypes.c_int
     lib.spv_process_batch_noalloc.argtypes = [BP, TP, P, P, ctypes.c_int, P, ctypes.c_int, CP, P]
     lib.spv_layout_batch.restype = ctypes.c_int
-    lib.spv_layout_batch.argtypes = [TP, i32, P, P, P]
+    lib.spv_layout_batch.argtypes = [TP, i32, P, P, P, sz, P]
+    lib.spv_layout_workspace_bytes.restype = sz
+    lib.spv_layout_workspace_bytes.argtypes = [i32, i64]
     lib.spv_op_layout.restype = ctypes.c_int
     lib.spv_op_layout.argtypes = [ctypes.c_uint32, P, P]
     lib.spv_autotune_batch.restype = ctypes.c_int
@@ -325,13 +327,18 @@ def autotune(words, mod_off, *, validate=True, encode=True, table=None, workspac
 LAYOUT_STATUS = ["OK", "SECTION_ORDER", "OUTSIDE_FUNCTION", "IN_FUNCTION", "BLOCK", "UNCLOSED"]
 
 
-def layout(table, n_modules, *, stream=None):
+def layout(table, n_modules, *, stream=None, workspace=None):
     """spv_layout_batch over a decoded table: (layout_status[M] int32,
-    layout_err_row[M] int64) device tensors."""
+    layout_err_row[M] int64) device tensors. workspace: a uint8 device tensor
+    of at least spv_layout_workspace_bytes bytes (allocated when None)."""
     dev = table.op.device
     status = torch.empty(max(1, n_modules), dtype=torch.int32, device=dev)
     err_row = torch.empty(max(1, n_modules), dtype=torch.int64, device=dev)
-    rc = load().spv_layout_batch(ctypes.byref(table.c()), n_modules, _ptr(status), _ptr(err_row), _stream(stream))
+    need = load().spv_layout_workspace_bytes(n_modules, table.capacity_rows)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(1, need), dtype=torch.uint8, device=dev)
+    rc = load().spv_layout_batch(ctypes.byref(table.c()), n_modules, _ptr(status), _ptr(err_row),
+                                 _ptr(workspace), workspace.numel(), _stream(stream))
     _check(rc, "spv_layout_batch")
     return status[:n_modules], err_row[:n_modules]
 

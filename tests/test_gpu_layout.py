@@ -115,3 +115,33 @@ def test_large_module(gpu):
     w, off, _, _ = synth.large_module(2, n_instr=400_000, n_funcs=50)
     st = check(gpu, w, off)
     assert int(st[0]) == 0
+
+
+def test_segmented_modules(gpu):
+    """Modules of more than 16,384 rows are checked in segments: errors in a
+    middle segment, right at segment starts and ends, in the last segment,
+    and a large module that ends inside a function, between small modules."""
+    big, boff, _, _ = synth.large_module(5, n_instr=120_000, n_funcs=10)
+    ins = instructions(big)
+    small, soff = synth.module_batch(4, 17)
+    smalls = [small[soff[i]:soff[i + 1]] for i in range(4)]
+
+    def rebuild(rows):
+        return H.module(rows, bound=int(big[3]), generator=int(big[2]))
+
+    variants = [ins]
+    for at in (16_384 - 1, 16_384, 32_768 + 7, 70_001, len(ins) - 3):
+        v = list(ins)
+        v.insert(at, H.ins(H.OpTypeVoid, 3))          # a type inside a function
+        variants.append(v)
+    v = list(ins)
+    v.insert(16_384 * 3, H.ins(H.OpLabel, 3))         # a label in an open block, at a segment start
+    variants.append(v)
+    variants.append(list(ins)[:50_000])               # the rows end inside a function
+    mods = []
+    for k, rows in enumerate(variants):
+        mods.append(smalls[k % 4])
+        mods.append(rebuild(rows))
+    words, offs = H.batch(mods)
+    st = check(gpu, words, offs)
+    assert (st[1::2] != 0).sum() == len(variants) - 1
