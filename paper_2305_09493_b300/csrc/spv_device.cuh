@@ -206,8 +206,24 @@ __device__ Walk walk_instruction(const WordFn &word, uint32_t wc, const spvt::Op
     if (d.fast & 1) {
         // only fixed ids / literals and a plain tail: a length check and a
         // range check of the id words (same result as the walk below)
-        const uint32_t need = 1u + d.nfixed, tail = d.fast >> 1;
-        r.ok = tail == 0 ? wc == need : (wc >= need && (tail != 3 || ((wc - need) & 1u) == 0));
+        const uint32_t need = 1u + d.nfixed, tail = (d.fast >> 1) & 7u;
+        if (tail == 4) {
+            // one bit-enum word: it and the literal parameters of its known
+            // bits must fill the instruction exactly
+            if (wc == need) r.ok = (d.fast & 16) != 0;
+            else if (wc > need) {
+                uint32_t x = word(need), np = 0;
+                while (x) {
+                    int b = __ffs(x) - 1;
+                    x &= x - 1;
+                    const spvt::EnDesc &e = T.benum[d.bkind][b];
+                    if (e.known) np += e.nparam;
+                }
+                r.ok = wc == need + 1u + np;
+            } else r.ok = false;
+        } else {
+            r.ok = tail == 0 ? wc == need : (wc >= need && (tail != 3 || ((wc - need) & 1u) == 0));
+        }
         if (r.ok) {
             uint32_t mask = d.id_mask;
             while (mask) {

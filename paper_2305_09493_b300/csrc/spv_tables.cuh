@@ -293,12 +293,13 @@ struct OpDesc {            // 16 bytes
     uint16_t name_off;
     uint8_t name_len;
     // fast form, for operand lists made only of fixed ids / literals and an
-    // optional id*, literal* or (id, id)* tail: bit0 set when it applies,
-    // bits 1-2 the tail (0 none, 1 ids, 2 literals, 3 id pairs)
+    // optional tail: bit0 set when it applies, bits 1-3 the tail (0 none,
+    // 1 ids, 2 literals, 3 id pairs, 4 one bit-enum word with its literal
+    // parameters), bit4 set when that bit-enum word may be absent
     uint8_t fast;
     uint16_t id_mask;      // bit i: word i (1 <= i <= nfixed) is an id
     uint8_t nfixed;        // words after the first word before the tail
-    uint8_t pad;
+    uint8_t bkind;         // bit-enum kind of tail 4
 };
 struct EnDesc {            // 8 bytes
     uint8_t known;
@@ -388,25 +389,32 @@ constexpr Tables build_tables()
         d.nprog = (uint8_t)np;
         // fast form
         {
-            bool fast = true;
+            bool fast = true, opt = false;
             int nfixed = 0, tail = 0;
+            uint8_t bkind = 0;
             uint16_t mask = 0;
             if (o.rt) { nfixed++; mask |= (uint16_t)(1u << nfixed); }
             if (o.rid) { nfixed++; mask |= (uint16_t)(1u << nfixed); }
             for (int k = 0; k < np; k++) {
                 uint8_t c = d.prog[k];
                 if (tail) { fast = false; break; }
+                const uint8_t cb = (uint8_t)(c & 0x7f);
                 if (c == A_ID) { nfixed++; mask |= (uint16_t)(1u << nfixed); }
                 else if (c == A_LIT) { nfixed++; }
                 else if (c == A_IDS) tail = 1;
                 else if (c == A_LITS) tail = 2;
+                else if (c == A_CTX) { nfixed++; tail = 2; }     // one literal word or more
                 else if (c == A_IDPAIRS) tail = 3;
+                else if (cb >= A_BITS && cb < A_BITS + NUM_BKINDS) {
+                    tail = 4; opt = (c & A_OPT) != 0; bkind = (uint8_t)(cb - A_BITS);
+                }
                 else { fast = false; break; }
             }
             if (nfixed > 15) fast = false;
-            d.fast = fast ? (uint8_t)(1 | (tail << 1)) : 0;
+            d.fast = fast ? (uint8_t)(1 | (tail << 1) | (opt ? 16 : 0)) : 0;
             d.id_mask = fast ? mask : 0;
             d.nfixed = fast ? (uint8_t)nfixed : 0;
+            d.bkind = fast ? bkind : 0;
         }
         t.layout[o.op] = LCL_BODY;
         int len = cstrlen(o.name);

@@ -423,6 +423,34 @@ def test_every_opcode_word_counts_and_operands(gpu):
     check(gpu, words, offs, dis=True)
 
 
+def test_trailing_bit_enum_and_context_literal_operands(gpu):
+    """Instructions ending in a bit-enum word (memory access of OpLoad and
+    OpStore, loop and selection controls) with every mix of known and unknown
+    bits and too few, exactly enough or too many parameter words, with the
+    word absent, and OpConstant with no literal or several: statuses, error
+    rows and text equal the oracle's."""
+    base = H.minimal_body()
+    fixed = {H.OpLoad: [2, 40, 4], H.OpStore: [4, 7], 246: [6, 6], 247: [6]}
+    masks = [0, 1, 2, 3, 4, 5, 6, 7, 8, 0x10, 0x20, 0x3f, 0xff, 0x100, 0x80000000, 0x41424344, 0xffffffff]
+    mods = []
+    for op, ids in fixed.items():
+        b = list(base)
+        b.insert(5, [((len(ids) + 1) << 16) | op] + ids)            # the bit-enum word absent
+        mods.append(H.module(b, bound=50))
+        for mask in masks:
+            for extra in range(5):
+                b = list(base)
+                b.insert(5, H.ins(op, ids, mask, [9] * extra))
+                mods.append(H.module(b, bound=50))
+    for n_lit in range(5):
+        b = list(base)
+        b.insert(8, H.ins(H.OpConstant, 2, 41, [5] * n_lit))
+        mods.append(H.module(b, bound=50))
+    words, offs = H.batch(mods)
+    g = check(gpu, words, offs, dis=True)
+    assert (g["status"] == 0).sum() >= 20 and (g["status"] != 0).sum() >= 20
+
+
 def _long_instruction_module(seed, n):
     """A valid module whose instructions include many longer than 32 words
     (wide struct types, phis with many pairs, long strings and names, calls
