@@ -311,8 +311,9 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             const bool stalled = (g == P.stall_tile);
             bool need_lookback = live && k > 0;
             if (need_lookback && !stalled) {
+                // the warp barrier orders every lane's map entry before lane
+                // 0's release, which makes them visible with the flag
                 P.tmap[g * NCAND + lane] = mv;
-                __threadfence();
                 __syncwarp();
                 if (lane == 0) st_release(&P.tstate[g], F_MAP);
             }
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                 bool gave_up = false;
                 for (;;) {
                     long long j = hi_j - lane;
-                    unsigned long long st = j >= first ? ld_acquire(&P.tstate[j]) : F_EXIT;
+                    unsigned long long st = j >= first ? ld_relaxed(&P.tstate[j]) : F_EXIT;
                     unsigned long long f = st & F_MASK;
                     unsigned exitm = __ballot_sync(0xffffffffu, j < first || f == F_EXIT);
                     unsigned nonem = __ballot_sync(0xffffffffu, j >= first && f == 0);
@@ -352,7 +353,10 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                     }
                     hi_j -= 32;
                 }
-                // apply predecessors' maps from the anchor forward
+                // apply predecessors' maps from the anchor forward; their F_MAP
+                // states were polled relaxed, so the map reads are ordered
+                // after the polls by one fence
+                fence_acq_rel();
                 uint32_t xx = ax;
                 for (long long t = anchor + 1; t < g && !gave_up; t += 8) {
                     uint32_t mrow[8];
@@ -371,7 +375,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                         unsigned long long st;
                         for (;;) {
                             st = 0;
-                            if (lane == 0) st = ld_acquire(&P.tstate[tt]);
+                            if (lane == 0) st = ld_relaxed(&P.tstate[tt]);
                             st = __shfl_sync(0xffffffffu, st, 0);
                             if ((st & F_MASK) == F_EXIT) break;
                             if (++spins > P.max_spins) { gave_up = true; break; }
@@ -400,8 +404,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                 s.exitp = xw;
                 if (live && g != P.stall_tile) {
                     uint32_t mx = xw == DEAD ? DEAD : xw + k * (uint32_t)T;
-                    __threadfence();
-                    st_release(&P.tstate[g], F_EXIT | (unsigned long long)mx);
+                    st_relaxed(&P.tstate[g], F_EXIT | (unsigned long long)mx);
                 }
             }
         }
@@ -451,7 +454,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             unsigned total = __shfl_sync(0xffffffffu, v, NW - 1);
             if (lane == 0) {
                 s.count = total;
-                if (!stalled) st_release(&P.cstate[g], (g == 0 ? F_EXIT : F_MAP) | total);
+                if (!stalled) st_relaxed(&P.cstate[g], (g == 0 ? F_EXIT : F_MAP) | total);
             }
         }
         __syncthreads();
@@ -478,7 +481,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                 bool gave_up = false;
                 for (;;) {
                     long long j = hi_j - lane;
-                    unsigned long long st = j >= 0 ? ld_acquire(&P.cstate[j]) : F_EXIT;
+                    unsigned long long st = j >= 0 ? ld_relaxed(&P.cstate[j]) : F_EXIT;
                     unsigned long long f = st & F_MASK;
                     unsigned exitm = __ballot_sync(0xffffffffu, f == F_EXIT);
                     unsigned nonem = __ballot_sync(0xffffffffu, f == 0);
@@ -497,7 +500,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                     hi_j -= 32;
                 }
                 if (gave_up) { excl = 0; if (lane == 0) s.timeout = 1; }
-                if (lane == 0 && !stalled) st_release(&P.cstate[g], F_EXIT | (excl + tile_count));
+                if (lane == 0 && !stalled) st_relaxed(&P.cstate[g], F_EXIT | (excl + tile_count));
             }
             if (lane == 0) {
                 s.row_base = excl;

@@ -770,7 +770,7 @@ __device__ void dis_lookback(const DP &P, MainSmem &s, long long t, uint32_t tot
         bool gave_up = false;
         for (;;) {
             long long jj = hi - lane;
-            unsigned long long st = jj >= 0 ? ld_acquire(&P.tstate[jj]) : F_INC;
+            unsigned long long st = jj >= 0 ? ld_relaxed(&P.tstate[jj]) : F_INC;
             unsigned long long f = st & F_MSK;
             unsigned incm = __ballot_sync(0xffffffffu, f == F_INC);
             unsigned nonem = __ballot_sync(0xffffffffu, f == 0);
@@ -789,7 +789,7 @@ __device__ void dis_lookback(const DP &P, MainSmem &s, long long t, uint32_t tot
             hi -= 32;
         }
         if (gave_up && lane == 0) { atomicExch(&P.ctrl->timeout, 1u); s.gave_up = 1; }
-        if (lane == 0 && t != P.stall_tile) st_release(&P.tstate[t], F_INC | (excl + total));
+        if (lane == 0 && t != P.stall_tile) st_relaxed(&P.tstate[t], F_INC | (excl + total));
     }
     if (lane == 0) {
         s.base = excl;
@@ -986,7 +986,7 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
         #pragma unroll
         for (int w = 0; w < DNT / 32; w++) total += s.warp_tot[w];
         // the tile's byte count, published before any wait of this tile
-        if (tid == 0 && t != P.stall_tile) st_release(&P.tstate[t], (t == 0 ? F_INC : F_AGG) | total);
+        if (tid == 0 && t != P.stall_tile) st_relaxed(&P.tstate[t], (t == 0 ? F_INC : F_AGG) | total);
         const bool last_tile = i0 + ITEMS >= n_items;
         const bool staged = total <= (uint32_t)TEXT_SMEM;
         auto format_item = [&](auto &k, int j) {
