@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(1024) k_prepass_scan(Params P)
 }
 
 // per tile: its record (owning module and where it starts), cleared
-// look-back states; clears the id arena
+// look-back states and map entries (0: not written); clears the id arena
 __global__ void k_tile_setup(Params P)
 {
     unsigned long long nt = P.ctrl->n_tiles;
@@ -185,6 +185,9 @@ __global__ void k_tile_setup(Params P)
         P.tile_rec[g] = r;
         P.tstate[g] = 0;
         P.cstate[g] = 0;
+        uint4 *mp = reinterpret_cast<uint4 *>(P.tmap + g * NCAND);
+        #pragma unroll
+        for (int i = 0; i < NCAND / 4; i++) mp[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     if (P.validate) {
         unsigned long long aw = P.ctrl->arena_used;
@@ -311,11 +314,14 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             const bool stalled = (g == P.stall_tile);
             bool need_lookback = live && k > 0;
             if (need_lookback && !stalled) {
-                // the warp barrier orders every lane's map entry before lane
-                // 0's release, which makes them visible with the flag
-                P.tmap[g * NCAND + lane] = mv;
+                // a map entry of a tile after a module's first is never 0 (an
+                // exit lies past the tile's start, DEAD and UNRES are not 0),
+                // so an entry read as 0 is not written yet: the entries need no
+                // ordering against the MAP state, which only tells the
+                // look-back that the map is on its way
+                st_relaxed32(&P.tmap[g * NCAND + lane], mv);
                 __syncwarp();
-                if (lane == 0) st_release(&P.tstate[g], F_MAP);
+                if (lane == 0) st_relaxed(&P.tstate[g], F_MAP);
             }
             // entry of this tile (module-relative)
             uint32_t entry;
@@ -353,15 +359,13 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                     }
                     hi_j -= 32;
                 }
-                // apply predecessors' maps from the anchor forward; their F_MAP
-                // states were polled relaxed, so the map reads are ordered
-                // after the polls by one fence
-                fence_acq_rel();
+                // apply predecessors' maps from the anchor forward; an entry
+                // read as 0 is not visible yet and is read again
                 uint32_t xx = ax;
                 for (long long t = anchor + 1; t < g && !gave_up; t += 8) {
                     uint32_t mrow[8];
                     #pragma unroll
-                    for (int q = 0; q < 8; q++) mrow[q] = (t + q < g) ? P.tmap[(t + q) * NCAND + lane] : 0u;
+                    for (int q = 0; q < 8; q++) mrow[q] = (t + q < g) ? ld_relaxed32(&P.tmap[(t + q) * NCAND + lane]) : 0u;
                     #pragma unroll
                     for (int q = 0; q < 8; q++) {
                         long long tt = t + q;
@@ -370,6 +374,12 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                         uint32_t tb = kt * (uint32_t)T;
                         uint32_t val = __shfl_sync(0xffffffffu, mrow[q], (int)((xx - tb) & 31u));
                         if (xx == DEAD || xx >= tb + (uint32_t)T) continue;
+                        while (xx - tb < 32 && val == 0u) {
+                            if (++spins > P.max_spins) { gave_up = true; break; }
+                            spin_pause();
+                            val = __shfl_sync(0xffffffffu, ld_relaxed32(&P.tmap[tt * NCAND + lane]), (int)((xx - tb) & 31u));
+                        }
+                        if (gave_up) break;
                         if (xx - tb < 32 && val != UNRES) { xx = val; continue; }
                         // the map cannot tell: wait for this tile's own exit
                         unsigned long long st;

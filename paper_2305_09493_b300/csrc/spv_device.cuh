@@ -113,28 +113,32 @@ __device__ __forceinline__ bool idset_contains(const uint32_t *base, uint32_t sl
 }
 
 // ---------------- memory ordering ----------------
-// Look-back states that carry their whole value in the state word are
-// written and polled with relaxed strong accesses: nothing else is read on
-// the strength of them. Only a state that guards other data (a tile map) is
-// published with a release store, and its reader orders its reads of that
-// data after its relaxed polls with one acquire-release fence. Acquire loads
-// in a poll loop, and fences on the publishing path, sit on the critical
-// path of every later tile.
+// Look-back states carry their whole value in the state word, and the
+// entries of a published tile map are each valid on their own (a map entry
+// is never 0 once written), so both are written and polled with relaxed
+// strong accesses: nothing is read on the strength of another location.
+// Acquire loads in a poll loop, and fences on the publishing path, would sit
+// on the critical path of every later tile.
 __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
 {
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ uint32_t ld_relaxed32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v)
 {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
+__device__ __forceinline__ void st_relaxed32(uint32_t *p, uint32_t v)
 {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ void spin_pause() { __nanosleep(32); }
 
 // ---------------- header ----------------
