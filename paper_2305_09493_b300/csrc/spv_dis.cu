@@ -809,20 +809,20 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n_items = (long long)P.ctrl->n_items;
     const long long ntiles = (n_items + ITEMS - 1) / ITEMS;
-    // tickets are taken one tile ahead; a ticket's holder is running, and a
-    // tile waits only on lower tiles, so the look-backs always end
-    unsigned int ticket = 0;
-    if (tid == 0) ticket = atomicAdd(&P.ctrl->next_tile, 1u);
+    // a ticket is taken when its tile starts: a tile waits only on lower
+    // tiles, whose holders are running, so the look-backs always end; a
+    // ticket taken a tile ahead would hold back every later tile's look-back
     for (;;) {
         // warp 0: the tile, its modules and their first items
         if (wid == 0) {
+            unsigned int ticket = 0;
+            if (lane == 0) ticket = atomicAdd(&P.ctrl->next_tile, 1u);
             const long long tt = (long long)__shfl_sync(0xffffffffu, ticket, 0);
             if (lane == 0) {
                 s.tile = tt;
                 s.gave_up = 0;
                 s.wlo = ~0ull;
                 s.whi = 0;
-                if (tt < ntiles) ticket = atomicAdd(&P.ctrl->next_tile, 1u);
             }
             if (tt < ntiles) {
                 const int m0 = P.tile_m0[tt];
