@@ -16,9 +16,11 @@
 //      Waits are bounded (max_spins) and end in SPV_TIMEOUT, never a hang.
 //   3. marks starts per segment, counts them and gets the tile's global row
 //      base from a second decoupled look-back (sum of predecessors' counts);
-//   4. writes one structure-of-arrays row per instruction, validates it
+//   4. writes one structure-of-arrays row per instruction and validates it
 //      (section 3.4.5 rules; ids below the bound and each result id set once,
-//      section 3.4.2) into per-tile aggregates, and re-encodes the tile.
+//      section 3.4.2) into per-tile aggregates.
+// The tile is re-encoded from its staged words by the other warps while
+// warp 0 runs the first look-back.
 // A prepass reads headers and lays out tiles and id bitmaps; a finalize pass
 // turns per-module aggregates into status codes; an exact fixup pass runs
 // only for modules with a duplicate result id or a missing capability.
@@ -417,6 +419,19 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                     st_relaxed(&P.tstate[g], F_EXIT | (unsigned long long)mx);
                 }
             }
+        } else if (P.out) {
+            // 5. encode, by the other warps while warp 0 looks back. In the
+            // fused path every field an instruction writes back (first word
+            // from wc/op, result type, result id) is decoded from the staged
+            // words themselves, so the re-encoded tile is the staged tile; the
+            // header bound is patched by the finalize pass.
+            uint32_t *dst = P.out + s.mod_base + (long long)k * T;
+            int n = live ? (int)tile_n : (int)(len_rel < (uint32_t)T ? len_rel : (uint32_t)T);
+            if (live) {
+                for (int i = tid - 32; i < n; i += NT - 32) dst[i] = s.w[pad(i)];
+            } else {
+                for (int i = tid - 32; i < n; i += NT - 32) dst[i] = __ldg(src + i);
+            }
         }
         __syncthreads();
         // 2e. per warp: entry of each 16-word segment (serial walk by lane 0)
@@ -600,19 +615,6 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             }
             uint32_t mx = __reduce_max_sync(0xffffffffu, ri);
             if (lane == 0 && mx) atomicMax(&s.max_rid, mx);
-        }
-        // 5. encode. In the fused path every field an instruction writes back
-        // (first word from wc/op, result type, result id) was just decoded from
-        // the staged words themselves, so the re-encoded tile is the staged
-        // tile; the header bound is patched by the finalize pass.
-        if (P.out) {
-            uint32_t *dst = P.out + s.mod_base + (long long)k * T;
-            int n = live ? (int)tile_n : (int)(len_rel < (uint32_t)T ? len_rel : (uint32_t)T);
-            if (live) {
-                for (int i = tid; i < n; i += NT) dst[i] = s.w[pad(i)];
-            } else {
-                for (int i = tid; i < n; i += NT) dst[i] = __ldg(src + i);
-            }
         }
         __syncthreads();
         // 6. flush the tile's aggregates to the module
