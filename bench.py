@@ -231,9 +231,9 @@ def cpu_baseline(words, mod_off, budget_s=12.0):
         oracle.encode(sub, off, d, True)
         oracle.disassemble(sub, off, True, True)
         dt = time.perf_counter() - t
-        if dt > budget_s / 3 or k == m_total or time.perf_counter() - t0 > budget_s:
+        if dt > budget_s / 2 or k == m_total or time.perf_counter() - t0 > 2 * budget_s:
             break
-        k = min(m_total, int(k * max(2.0, budget_s / 2 / max(dt, 1e-3))))
+        k = min(m_total, int(k * max(2.0, budget_s / max(dt, 1e-3))))
     gbs = 4 * len(sub) / dt / 1e9
     return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": f"first {k} of {m_total} modules ({len(sub)} words): decode+validate+encode+disassemble, "
