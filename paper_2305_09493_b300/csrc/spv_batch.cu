@@ -223,6 +223,7 @@ struct TileSmem {
     // aggregates flushed once per tile
     unsigned long long err_key;
     uint32_t n_cap, n_mm, n_ep, n_fn, decl_lo, decl_hi, req_lo, req_hi, max_rid, flags, n_ids;
+    unsigned int vnext;                             // next row chunk to validate
 };
 
 template <int NT, int L>
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                 s.err_key = NO_KEY;
                 s.n_cap = s.n_mm = s.n_ep = s.n_fn = 0;
                 s.decl_lo = s.decl_hi = s.req_lo = s.req_hi = 0;
-                s.max_rid = 0; s.flags = 0; s.n_ids = 0;
+                s.max_rid = 0; s.flags = 0; s.n_ids = 0; s.vnext = 0;
             }
         }
         __syncthreads();
@@ -497,7 +498,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
         __syncthreads();
         // 4a. warp 0: the tile's first row (decoupled look-back over all tiles'
         //     counts); meanwhile the other warps validate the tile's rows,
-        //     which needs no global row index
+        //     which needs no global row index, and warp 0 joins them after
         if (wid == 0) {
             unsigned long long excl = 0;
             if (g > 0) {
@@ -532,12 +533,20 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                 if (k == 0) P.first_row[m] = (int64_t)excl;
                 if (g == n_tiles - 1) P.ctrl->total_rows = excl + tile_count;
             }
-        } else if (P.validate) {
+        }
+        if (P.validate) {
+            // rows in chunks of 32 from a shared counter: warp 0 joins when
+            // its look-back is done, and a slow chunk holds back no warp's
+            // later rows
             const uint32_t bound = P.ms[m].bound;
             const long long arena_off = P.ms[m].arena_off;
             const uint32_t id_slots = P.ms[m].id_slots;
-            for (unsigned rb = 0; rb < tile_count; rb += NT - 32) {
-                const unsigned r = rb + (unsigned)(tid - 32);
+            for (;;) {
+                unsigned rb = 0;
+                if (lane == 0) rb = atomicAdd(&s.vnext, 32u);
+                rb = __shfl_sync(0xffffffffu, rb, 0);
+                if (rb >= tile_count) break;
+                const unsigned r = rb + (unsigned)lane;
                 uint32_t ri = 0;
                 uint64_t req = 0;
                 uint32_t inserted = 0;
