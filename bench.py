@@ -215,7 +215,7 @@ def serve_leg(spvgpu, w_np, off_np, rate, seconds, max_batch_modules=0, pool_siz
             "admission_retries": int(busy)}
 
 
-def cpu_baseline(words, mod_off, budget_s=12.0):
+def cpu_baseline(words, mod_off, budget_s=15.0):
     """The oracle (plain sequential C, one thread) on a bounded sample: the
     first modules of the batch, as many as fit the time budget."""
     import oracle
