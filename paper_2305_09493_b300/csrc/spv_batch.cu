@@ -560,10 +560,12 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                         uint32_t q = (d.flags & 2) ? 2u : 1u;
                         if (q < wc) ri = word(p + q);
                     }
-                    if (op == 17) { atomicAdd(&s.n_cap, 1u); if (wc >= 2) { uint32_t c = word(p + 1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); } }
-                    else if (op == 14) atomicAdd(&s.n_mm, 1u);
-                    else if (op == 15) atomicAdd(&s.n_ep, 1u);
-                    else if (op == 54) atomicAdd(&s.n_fn, 1u);
+                    if (d.flags & 8) {            // the few opcodes validation counts or measures
+                        if (op == 17) { atomicAdd(&s.n_cap, 1u); if (wc >= 2) { uint32_t c = word(p + 1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); } }
+                        else if (op == 14) atomicAdd(&s.n_mm, 1u);
+                        else if (op == 15) atomicAdd(&s.n_ep, 1u);
+                        else if (op == 54) atomicAdd(&s.n_fn, 1u);
+                    }
                     if (!known) { atomicMin(&s.err_key, make_key(r, R_UNKNOWN, 0)); }
                     else {
                         auto iw = [&](uint32_t i) -> uint32_t { return word(p + i); };
@@ -581,7 +583,8 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                                     atomicOr(&s.flags, MF_DUP);
                                 }
                             }
-                            req = wk.req | width_caps(iw, op, wc);
+                            req = wk.req;
+                            if (d.flags & 8) req |= width_caps(iw, op, wc);
                         }
                     }
                 }

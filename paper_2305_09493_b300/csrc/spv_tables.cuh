@@ -286,7 +286,7 @@ constexpr CapDep CAP_DEPS[] = {
 
 // ---- dense compiled tables ----------------------------------------------------
 struct OpDesc {            // 16 bytes
-    uint8_t flags;         // bit0 known, bit1 has result type, bit2 has result id
+    uint8_t flags;         // bit0 known, bit1 has result type, bit2 has result id, bit3 counted by validation
     int8_t cap;            // required capability or -1
     uint8_t nprog;
     uint8_t prog[5];
@@ -382,7 +382,10 @@ constexpr Tables build_tables()
     Tables t{};
     for (const OpSrc &o : OP_LIST) {
         OpDesc &d = t.ops[o.op];
-        d.flags = (uint8_t)(1 | (o.rt ? 2 : 0) | (o.rid ? 4 : 0));
+        // bit 3: validation counts the instruction (capability, memory model,
+        // entry point, function) or reads its width (integer and float types)
+        const bool counted = o.op == 14 || o.op == 15 || o.op == 17 || o.op == 21 || o.op == 22 || o.op == 54;
+        d.flags = (uint8_t)(1 | (o.rt ? 2 : 0) | (o.rid ? 4 : 0) | (counted ? 8 : 0));
         d.cap = o.cap;
         int np = 0;
         for (int k = 0; k < 5; k++) if (o.p[k]) d.prog[np++] = o.p[k];
