@@ -293,8 +293,10 @@ def run_reference(args):
         last.pop("k", None)
         vals.append(last["value"])
     v = float(np.median(vals))
+    # a step's time over the whole workload at the sampled rate
+    ms_step = 1e3 * 4.0 * len(w) / (v * 1e9) if v > 0 else None
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": last["sample"], "value": v, "unit": "GB/s"},
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
