@@ -1326,6 +1326,14 @@ __device__ __forceinline__ unsigned long long measure_line(const AsmP &P, long l
     return (unsigned long long)lw | ((unsigned long long)lnm << 20) | ((unsigned long long)fl << 40);
 }
 
+
+// one 16-byte asynchronous copy from global to shared memory (both
+// addresses 16-byte aligned), completed by cp.async.wait_all
+__device__ __forceinline__ void stage16(void *dst, const void *src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
 __global__ void __launch_bounds__(MT_THREADS, 3) k_asm_measure(AsmP P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1344,7 +1352,7 @@ __global__ void __launch_bounds__(MT_THREADS, 3) k_asm_measure(AsmP P)
         for (long long k = threadIdx.x; a_al + 16 * k < se; k += MT_THREADS) {
             const long long g = a_al + 16 * k;
             if (g >= a && g + 16 <= se) {
-                *reinterpret_cast<uint4 *>(S.text + 16 * k) = *reinterpret_cast<const uint4 *>(P.text + g);
+                stage16(S.text + 16 * k, P.text + g);      // one round trip for the whole tile
             } else {
                 for (int j = 0; j < 16; j++) {
                     const long long q = g + j;
@@ -1352,6 +1360,7 @@ __global__ void __launch_bounds__(MT_THREADS, 3) k_asm_measure(AsmP P)
                 }
             }
         }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
         for (int i = threadIdx.x; i < MT_KEYS; i += MT_THREADS) S.hist[i] = 0;
         __syncthreads();
         // each line's length (up to the next line start, less its '\n'),
@@ -1360,7 +1369,7 @@ __global__ void __launch_bounds__(MT_THREADS, 3) k_asm_measure(AsmP P)
         for (int i = threadIdx.x; i < nt; i += MT_THREADS) {
             const long long q = (long long)P.ls[l0 + i];
             long long qe = i + 1 < nt ? (long long)P.ls[l0 + i + 1] : e;
-            if (qe > q && P.text[qe - 1] == '\n') qe--;
+            if (qe > q && (qe <= se ? S.text[qe - 1 - a_al] : P.text[qe - 1]) == '\n') qe--;
             const long long n = qe - q;
             const int m = P.lmod[l0 + i];
             const bool live = n > 0 && (P.mod[m].flags & MF_FIT_LINES);
