@@ -114,7 +114,10 @@ typedef struct spv_config {
     int64_t max_spins;          /* bound on every wait inside a kernel (0: default 1 << 20 polls); a
                                    wait that runs out ends with SPV_TIMEOUT for every module of the call */
     int64_t test_stall_tile;    /* test hook, 0 = off: with n > 0, tile n-1 never publishes its look-back
-                                   states, so the waits of the tiles after it run out */
+                                   states, so the waits of the tiles after it run out; with n < 0, tile
+                                   -n-1 announces its tile map but never writes the map's entries, its
+                                   exit or its row count, so a later tile of its module waits on a map
+                                   entry that nothing writes */
 } spv_config;
 
 /* Workspace bytes needed by spv_process_batch / spv_decode_batch /

@@ -71,6 +71,8 @@ struct Params {
     int64_t *abase;                // [n_modules + 1] prefix of the id-set words each module asks for
     long long max_spins;
     long long stall_tile;          // test hook: this tile never publishes its look-back states (-1: none)
+    long long stall_map_tile;      // test hook: this tile publishes its MAP state but never its map entries,
+                                   // exit or row count (-1: none)
     int persistent;
     int table_mode;                // validating a caller's table: never write its columns
     int tile_words;                // words per tile of k_tile
@@ -315,6 +317,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             uint32_t mv = (x == DEAD || x == UNRES) ? x : x + k * (uint32_t)T;
             long long first = g - (long long)k;
             const bool stalled = (g == P.stall_tile);
+            const bool map_only = (g == P.stall_map_tile);
             bool need_lookback = live && k > 0;
             if (need_lookback && !stalled) {
                 // a map entry of a tile after a module's first is never 0 (an
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                 // so an entry read as 0 is not written yet: the entries need no
                 // ordering against the MAP state, which only tells the
                 // look-back that the map is on its way
-                st_relaxed32(&P.tmap[g * NCAND + lane], mv);
+                if (!map_only) st_relaxed32(&P.tmap[g * NCAND + lane], mv);
                 __syncwarp();
                 if (lane == 0) st_relaxed(&P.tstate[g], F_MAP);
             }
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                 }
                 s.entry = x0;
                 s.exitp = xw;
-                if (live && g != P.stall_tile) {
+                if (live && g != P.stall_tile && g != P.stall_map_tile) {
                     uint32_t mx = xw == DEAD ? DEAD : xw + k * (uint32_t)T;
                     st_relaxed(&P.tstate[g], F_EXIT | (unsigned long long)mx);
                 }
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
         for (int d = 1; d < 32; d <<= 1) { unsigned v = __shfl_up_sync(0xffffffffu, incl, d); if (lane >= d) incl += v; }
         if (lane == 31) s.warp_tot[wid] = incl;
         __syncthreads();
-        const bool stalled = (g == P.stall_tile);
+        const bool stalled = (g == P.stall_tile || g == P.stall_map_tile);
         if (wid == 0) {                          // block scan of the warp counts; publish the tile's count
             unsigned v = lane < NW ? s.warp_tot[lane] : 0;
             #pragma unroll
@@ -979,7 +982,7 @@ Layout make_layout(int n_mod, long long n_words, long long arena_words, int tile
     return L;
 }
 
-struct Cfg { int T, NT, L, ctas_per_sm, per_module; long long max_spins, stall_tile; };
+struct Cfg { int T, NT, L, ctas_per_sm, per_module; long long max_spins, stall_tile, stall_map_tile; };
 
 // A tile shape left unset (tile_words and threads both 0) follows the batch:
 // batches of small modules (mean under 4,096 words) take 2,048-word tiles
@@ -987,17 +990,18 @@ struct Cfg { int T, NT, L, ctas_per_sm, per_module; long long max_spins, stall_t
 // 1,000-module bins of 200 to 50,000 instructions).
 int resolve_cfg(const spv_config *c, Cfg *out, int n_modules, long long n_words)
 {
-    Cfg r{4096, 256, 16, 0, 0, 1LL << 20, -1};
+    Cfg r{4096, 256, 16, 0, 0, 1LL << 20, -1, -1};
     const bool auto_shape = !c || (!c->tile_words && !c->threads);
     if (auto_shape && n_modules > 0 && n_words / n_modules < 4096) { r.T = 2048; r.NT = 128; }
     if (c) {
         if (c->tile_words) r.T = c->tile_words;
         if (c->threads) r.NT = c->threads;
-        if (c->ctas_per_sm < 0 || c->max_spins < 0 || c->test_stall_tile < 0) return SPV_E_ARG;
+        if (c->ctas_per_sm < 0 || c->max_spins < 0) return SPV_E_ARG;
         r.ctas_per_sm = c->ctas_per_sm;
         r.per_module = c->per_module;
         if (c->max_spins) r.max_spins = c->max_spins;
-        r.stall_tile = c->test_stall_tile - 1;
+        if (c->test_stall_tile > 0) r.stall_tile = c->test_stall_tile - 1;
+        if (c->test_stall_tile < 0) r.stall_map_tile = -c->test_stall_tile - 1;
     }
     if (r.NT != 128 && r.NT != 256 && r.NT != 512) return SPV_E_ARG;
     if (r.T % r.NT) return SPV_E_ARG;
@@ -1067,6 +1071,8 @@ Params base_params(const spv_batch *b, void *ws, const Layout &L, int tile_words
 {
     Params P{};
     P.tile_words = tile_words;
+    P.stall_tile = -1;                 // test hooks off unless a call sets them
+    P.stall_map_tile = -1;
     char *w = (char *)ws;
     P.words = b->words; P.mod_off = b->mod_off; P.n_modules = b->n_modules;
     P.ctrl = (Ctrl *)(w + L.ctrl);
@@ -1130,6 +1136,7 @@ extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint3
     P.out = out_words; P.validate = validate ? 1 : 0; P.recompute_bound = recompute_bound ? 1 : 0;
     P.max_spins = c.max_spins;
     P.stall_tile = c.stall_tile;
+    P.stall_map_tile = c.stall_map_tile;
     SPV_LAUNCH("k_prepass_mod", st, k_prepass_mod<<<sm_count() * 4, 256, 0, st>>>(P, c.T));
     SPV_LAUNCH("k_prepass_scan", st, k_prepass_scan<<<1, 1024, 0, st>>>(P));
     int nsm = sm_count();
@@ -1242,6 +1249,7 @@ extern "C" int spv_validate_batch(const spv_batch *batch, const spv_table *table
     P.table_mode = 1;
     P.max_spins = c.max_spins;
     P.stall_tile = -1;
+    P.stall_map_tile = -1;
     int nsm = sm_count();
     int nb = (batch->n_modules + 255) / 256;
     SPV_LAUNCH("k_prepass_mod", st, k_prepass_mod<<<sm_count() * 4, 256, 0, st>>>(P, c.T));

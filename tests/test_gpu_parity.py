@@ -364,6 +364,18 @@ def test_bounded_wait_times_out_without_hanging(gpu):
     check(gpu, w, off)
 
 
+def test_map_entry_wait_times_out_without_hanging(gpu):
+    """A tile that announces its tile map but never writes the entries (nor
+    its exit or row count): the later tile that applies that map polls an
+    entry that nothing writes, gives up after max_spins, and every module
+    reports the timeout; the next call on the same context is exact."""
+    w, off, _, _ = synth.large_module(6, n_instr=60_000, n_funcs=4)
+    cfg = gpu.make_config(tile_words=1024, threads=128, max_spins=2000, test_stall_tile=-6)
+    g = run(gpu, w, off, cfg=cfg)
+    assert gpu.STATUS[g["status"][0]] == "TIMEOUT"
+    check(gpu, w, off)
+
+
 def test_text_lookback_times_out_without_hanging(gpu):
     """A text tile that never publishes its byte count (the test hook): the
     look-backs of the tiles after it give up after max_spins polls, every
