@@ -572,7 +572,11 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                     if (!known) { atomicMin(&s.err_key, make_key(r, R_UNKNOWN, 0)); }
                     else {
                         auto iw = [&](uint32_t i) -> uint32_t { return word(p + i); };
-                        Walk wk = walk_instruction(iw, wc, d, bound);
+                        // an instruction wholly inside the staged words (almost every one) reads
+                        // them without the per-word range check
+                        auto sw = [&](uint32_t i) -> uint32_t { return s.w[pad((int)(p + i))]; };
+                        Walk wk = p + wc <= (uint32_t)(T + HALO) ? walk_instruction(sw, wc, d, bound)
+                                                                  : walk_instruction(iw, wc, d, bound);
                         if (!wk.ok) atomicMin(&s.err_key, make_key(r, R_BADOP, 0));
                         else if (wk.oob) atomicMin(&s.err_key, make_key(r, R_OOB, 0));
                         else {
