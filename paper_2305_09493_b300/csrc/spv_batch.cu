@@ -40,6 +40,7 @@ using namespace spvd;
 namespace {
 
 constexpr int HALO = 64;          // words staged past the tile end
+static_assert(HALO >= 3, "a start's result type and id are read from the staged words");
 constexpr int NCAND = 32;         // candidate entries in a tile map
 constexpr uint16_t NONE16 = 0xFFFF;
 constexpr unsigned long long F_MAP = 1ull << 62, F_EXIT = 2ull << 62, F_MASK = 3ull << 62;
@@ -555,13 +556,13 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                 uint32_t inserted = 0;
                 if (r < tile_count) {
                     uint32_t p = S16[r];
-                    uint32_t w0 = word(p);
+                    uint32_t w0 = s.w[pad((int)p)];           // staged: p lies in the tile
                     uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
                     const spvt::OpDesc &d = TB.ops[op < 256 ? op : 0];
                     bool known = op < 256 && (d.flags & 1);
                     if (known && (d.flags & 4)) {
                         uint32_t q = (d.flags & 2) ? 2u : 1u;
-                        if (q < wc) ri = word(p + q);
+                        if (q < wc) ri = s.w[pad((int)(p + q))]; // within the halo
                     }
                     if (d.flags & 8) {            // the few opcodes validation counts or measures
                         if (op == 17) { atomicAdd(&s.n_cap, 1u); if (wc >= 2) { uint32_t c = word(p + 1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); } }
@@ -613,15 +614,17 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             const unsigned r = rb + tid;
             uint32_t ri = 0;
             if (r < tile_count) {
+                // a start lies in the tile and the result type and id within two
+                // words of it, inside the 64-word halo: staged, read directly
                 uint32_t p = S16[r];
-                uint32_t w0 = word(p);
+                uint32_t w0 = s.w[pad((int)p)];
                 uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
                 const spvt::OpDesc &d = TB.ops[op < 256 ? op : 0];
                 uint32_t rt = 0;
                 if (op < 256 && (d.flags & 1)) {
                     uint32_t q = 1;
-                    if (d.flags & 2) { if (q < wc) rt = word(p + q); q++; }
-                    if (d.flags & 4) { if (q < wc) ri = word(p + q); }
+                    if (d.flags & 2) { if (q < wc) rt = s.w[pad((int)(p + q))]; q++; }
+                    if (d.flags & 4) { if (q < wc) ri = s.w[pad((int)(p + q))]; }
                 }
                 unsigned long long row = row_base + r;
                 if ((long long)row < P.cap_rows) {
