@@ -167,7 +167,11 @@ int spv_process_batch(const spv_batch *batch, spv_table *table, uint32_t *status
  * library holds until the process exits. Nothing is allocated by the call.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture. The address is kept per device together
+ *     with the context it was found in, and looked up again when a call runs
+ *     in another context (after cudaDeviceReset, say).
+ *   - Arguments are checked first, as by spv_process_batch (SPV_E_ARG), then
+ *     the scratch size.
  *   - A batch whose workspace (spv_workspace_bytes with the default arena)
  *     exceeds SPV_NOALLOC_SCRATCH_BYTES is rejected with SPV_E_WORKSPACE and
  *     nothing is launched; cfg->per_module is rejected with
@@ -546,20 +550,30 @@ int spv_pipe_run(spv_pipe *p, const uint32_t *h_words, int64_t n_words, const in
 /* Wait for the handle's streams, free its buffers and streams. */
 void spv_pipe_destroy(spv_pipe *p);
 
-/* Host-side queries of the library's own opcode / enumerant tables (no GPU
- * needed). spv_op_info returns 0 and fills the outputs for a known opcode,
- * -1 otherwise; cap is the capability the opcode requires or -1. */
 /* Sizes of a batch's outputs (a convenience for sizing buffers):
  * *rows_upper (may be NULL) = n_words - 5 * n_modules, at least 0, an upper
  * bound of the decoded rows from the batch's shape alone (an instruction
  * holds at least one word, a header five). *text_bytes (may be NULL) = the
  * exact size of spv_disassemble_batch's text with these options, found by
- * decoding and measuring the batch on the stream with scratch the call
- * allocates (cudaMallocAsync) and frees; with text_bytes the call is
- * synchronous. Returns SPV_SUCCESS or an SPV_E_* code. */
+ * decoding and measuring the batch on the stream.
+ * EXCEPTION to the conventions of every other call in this header: when
+ * text_bytes is given, this call ALLOCATES its own device scratch
+ * (cudaMallocAsync on the stream, freed with cudaFreeAsync before it
+ * returns) and is SYNCHRONOUS (it waits for the stream to read the size
+ * back). It is a sizing helper for setting up buffers, not a hot-path call:
+ * do not use it inside a stream capture or where allocation is forbidden;
+ * there, size the text buffer from spv_disassemble_batch itself (its
+ * text_off[n_modules] is the needed size even when it exceeds
+ * text_capacity, and a call with text_capacity 0 writes no text). With
+ * text_bytes NULL the call only
+ * computes rows_upper on the host and touches no device state.
+ * Returns SPV_SUCCESS or an SPV_E_* code. */
 int spv_query_sizes(const spv_batch *batch, const spv_dis_opts *opts, int64_t *rows_upper, uint64_t *text_bytes,
                     spv_stream_t stream);
 
+/* Host-side queries of the library's own opcode / enumerant tables (no GPU
+ * needed). spv_op_info returns 0 and fills the outputs for a known opcode,
+ * -1 otherwise; cap is the capability the opcode requires or -1. */
 int spv_op_info(uint32_t opcode, int *has_rtype, int *has_rid, int *cap, const char **name);
 /* kind is one of the enumeration names used by the operand lists
  * ("Capability", "Decoration", ...). Returns 0 for a known enumerant. */

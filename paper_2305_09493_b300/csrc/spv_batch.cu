@@ -1305,15 +1305,45 @@ namespace {
 // Every GPU that loads this library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SPV_NOALLOC_SCRATCH_BYTES];
 std::mutex g_noalloc_mu;
-void *g_noalloc_addr[1024];   // per device: the array's device address (host code cannot use its name)
+// Per device: the array's device address (host code cannot use its name) and
+// the context it was looked up in. A context torn down and made again (for
+// example after cudaDeviceReset) loads the module again, and the array may
+// then sit elsewhere, so the address is looked up again whenever the current
+// context differs from the cached one.
+struct NoallocSlot { void *addr; void *ctx; };
+NoallocSlot g_noalloc_slot[1024];
+typedef int (*CtxGetCurrentFn)(void **);
+CtxGetCurrentFn g_ctx_get_current;     // the driver's cuCtxGetCurrent, found once
+bool g_ctx_lookup_done;
+
+void *current_context()
+{
+    if (!g_ctx_lookup_done) {
+        g_ctx_lookup_done = true;
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = (CtxGetCurrentFn)fn;
+    }
+    void *ctx = nullptr;
+    if (!g_ctx_get_current || g_ctx_get_current(&ctx) != 0) return nullptr;
+    return ctx;
+}
 }  // namespace
 
 extern "C" int spv_process_batch_noalloc(const spv_batch *batch, spv_table *table, uint32_t *status,
                                          int64_t *err_row, int validate, uint32_t *out_words,
                                          int recompute_bound, const spv_config *cfg, spv_stream_t stream)
 {
+    // the argument checks of spv_process_batch come first, so a bad argument
+    // is SPV_E_ARG whatever the batch's size
     Cfg c;
-    if (!check_batch(batch) || resolve_cfg(cfg, &c, batch->n_modules, batch->n_words)) return SPV_E_ARG;
+    if (!check_batch(batch) || !table || !status || !err_row || resolve_cfg(cfg, &c, batch->n_modules, batch->n_words))
+        return SPV_E_ARG;
+    if (!table->op || !table->wc || !table->off || !table->rtype || !table->rid || !table->mod ||
+        !table->mod_first_row || !table->mod_n_instr || table->capacity_rows < 0)
+        return SPV_E_ARG;
     if (c.per_module) return SPV_E_UNSUPPORTED;
     if (make_layout(batch->n_modules, batch->n_words, 0, c.T).total > (size_t)SPV_NOALLOC_SCRATCH_BYTES)
         return SPV_E_WORKSPACE;
@@ -1321,14 +1351,18 @@ extern "C" int spv_process_batch_noalloc(const spv_batch *batch, spv_table *tabl
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 1024) return SPV_E_CUDA;
     void *scratch = nullptr;
     {
-        // set-up, once per device, with that device current
+        // set-up, once per device (and again after its context is made anew),
+        // with that device current
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
+        void *ctx = current_context();          // null before the runtime has made one current
+        NoallocSlot &sl = g_noalloc_slot[dev];
+        if (!sl.addr || !ctx || ctx != sl.ctx) {
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SPV_E_CUDA;
-            g_noalloc_addr[dev] = p;
+            sl.addr = p;
+            sl.ctx = current_context();         // the context the lookup ran in
         }
-        scratch = g_noalloc_addr[dev];
+        scratch = sl.addr;
     }
     // the kernels initialise every part of the scratch they read (look-back
     // states, counters, module states and id sets are cleared on the device

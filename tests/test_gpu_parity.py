@@ -393,6 +393,10 @@ def test_text_lookback_times_out_without_hanging(gpu):
 # full-size workloads
 # ---------------------------------------------------------------------------
 def test_full_size_batch_10k_modules(gpu):
+    """The benchmark's batch of 10,000 modules (122M words) at full size:
+    table, statuses, encoded words, and the whole disassembly with inline
+    names and header lines (about 830 MB of text) with its offsets, byte for
+    byte against the oracle."""
     w, off = synth.module_batch(10_000, 0)
     g = run(gpu, w, off)
     d = oracle.decode(w, off)
@@ -400,6 +404,8 @@ def test_full_size_batch_10k_modules(gpu):
     st, er = oracle.validate(w, off)
     assert np.array_equal(g["status"], st) and np.array_equal(g["err_row"], er)
     assert np.array_equal(g["out"], oracle.encode(w, off, d, True))
+    del d
+    check_dis(gpu, w, off, g, modes=((True, True),))
 
 
 def test_full_size_large_module_and_text(gpu):
