@@ -103,9 +103,10 @@ typedef struct spv_table {
 
 /* Tuning of the batched kernels; zero fields take defaults. */
 typedef struct spv_config {
-    int32_t tile_words;         /* words per tile: 1024, 2048, 4096 or 8192 */
-    int32_t threads;            /* threads per CTA: 128, 256 or 512; tile_words/threads must be 8 or 16, and
-                                   512 threads only with 16. Both 0 (default): 2048 x 128 for batches whose
+    int32_t tile_words;         /* words per tile: 512, 1024, 2048, 4096 or 8192 */
+    int32_t threads;            /* threads per CTA: 64, 128, 256 or 512; tile_words/threads must be 8 or 16,
+                                   512 threads only with 16 and 64 only with 8. Tiles start on 16-byte
+                                   boundaries of the word buffer. Both 0 (default): 2048 x 128 for batches whose
                                    mean module is under 4,096 words, else 4096 x 256; one of them 0: that one
                                    takes its default (4096 words, 256 threads) */
     int32_t ctas_per_sm;        /* resident CTAs per SM for the persistent grid (default: occupancy maximum) */

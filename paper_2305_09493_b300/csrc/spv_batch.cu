@@ -44,16 +44,21 @@ static_assert(HALO >= 3, "a start's result type and id are read from the staged 
 constexpr int NCAND = 32;         // candidate entries in a tile map
 constexpr uint16_t NONE16 = 0xFFFF;
 constexpr unsigned long long F_MAP = 1ull << 62, F_EXIT = 2ull << 62, F_MASK = 3ull << 62;
+// a tile whose guessed starts form a chain publishes, beside its map, the
+// state F_FMAP: bits 0-31 mark the candidate entries that leave the tile at
+// the guessed chain's exit, bits 32-49 hold that exit (tile-local), so a
+// later tile entering at a marked candidate needs no map entry
+constexpr unsigned long long F_FMAP = 3ull << 62;
 
-__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }   // one spare word per 16: conflict-free segments
 
 // What a tile of k_tile needs to know about itself, one 32-byte load.
 struct TileRec {
     long long base;          // the module's first word
     uint32_t m, k;           // module, tile index within the module
-    uint32_t len_rel;        // module words from this tile's first word (0 for a module too large)
+    uint32_t len_rel;        // the module's end, counted from the tile's first staged word (0: a module too large)
     uint32_t hdr;            // the module's header status
-    uint32_t pad[2];
+    uint32_t ph;             // words from the 16-byte boundary below the module's first word to that word
+    uint32_t pad;
 };
 
 struct Params {
@@ -77,7 +82,14 @@ struct Params {
     int persistent;
     int table_mode;                // validating a caller's table: never write its columns
     int tile_words;                // words per tile of k_tile
+    int out_vec;                   // out and words share their 16-byte phase: 16-byte stores
 };
+
+// words from the 16-byte boundary below word o of the batch to that word
+__host__ __device__ inline uint32_t word_phase(const uint32_t *words, long long o)
+{
+    return (uint32_t)((((unsigned long long)(uintptr_t)words) >> 2) + (unsigned long long)o) & 3u;
+}
 
 // ---------------------------------------------------------------------------
 // prepass, in two kernels: per module (many CTAs) the header status, bound,
@@ -95,7 +107,10 @@ __global__ void k_prepass_mod(Params P, int tile_words)
         if (len < 0 || len > 0x7fffffffLL) { hdr = S_CAPACITY; flags = MF_CAPACITY; len = 0; }
         else hdr = header_status(P.words + o, len);
         if (len >= 4) bound = P.words[o + 3];
-        nt = len > 0 ? ((unsigned long long)len + (unsigned)tile_words - 1) >> (31 - __clz(tile_words)) : 1;  // tile_words: a power of two
+        // tiles start on 16-byte boundaries: the first one also holds the
+        // ph words below the module's first word
+        const uint32_t ph = word_phase(P.words, o);
+        nt = len > 0 ? ((unsigned long long)len + ph + (unsigned)tile_words - 1) >> (31 - __clz(tile_words)) : 1;  // tile_words: a power of two
         if (hdr == S_OK && P.validate) nb = idset_words(bound, len);
         P.tile_off[m] = (int64_t)nt;              // counts; k_prepass_scan makes them offsets
         P.abase[m] = (int64_t)nb;
@@ -184,7 +199,8 @@ __global__ void k_tile_setup(Params P)
         r.k = (uint32_t)(g - P.tile_off[lo]);
         r.base = P.mod_off[lo];
         r.hdr = P.ms[lo].hdr;
-        long long lr = (P.mod_off[lo + 1] - r.base) - (long long)r.k * P.tile_words;
+        r.ph = word_phase(P.words, r.base);
+        long long lr = (P.mod_off[lo + 1] - r.base) + r.ph - (long long)r.k * P.tile_words;
         if (r.hdr == S_CAPACITY) lr = 0;
         r.len_rel = (uint32_t)(lr < 0 ? 0 : lr);
         P.tile_rec[g] = r;
@@ -203,23 +219,57 @@ __global__ void k_tile_setup(Params P)
 
 // ---------------------------------------------------------------------------
 // the fused tile kernel
+//
+// Tiles sit on 16-byte boundaries of the word buffer: when a module's first
+// word lies ph words past such a boundary, its tile k covers the module
+// positions [k*T - ph, (k+1)*T - ph). Every tile, and every thread's
+// segment of L words, is then staged and read with 16-byte copies. Inside a
+// tile positions are tile-local (0 .. T-1); published exits and map entries
+// are module positions.
+//
+// Instruction starts (section 3.4.6: an instruction's first word holds its
+// word count) form the chain p -> p + wc(p). The kernel first guesses the
+// tile's starts word by word: a word is a candidate start when its opcode is
+// in the table and its word count fits that opcode's operand list. The
+// guess is kept only if it is itself a chain: every candidate's successor
+// is the next candidate, except one whose successor leaves the tile (counts
+// of successor marks against candidates, over the whole tile). A chain that
+// holds the tile's true entry gives every start from that entry on. Any
+// other case (a framing error, an unknown opcode, a wrong operand count, or
+// a word that merely looks like a start and breaks the chain) takes the
+// exact path: per-segment exits by a backward pass, warp maps, and walks.
 // ---------------------------------------------------------------------------
+template <int L> __device__ __forceinline__ int pw(int i) { return i + 4 * (i / L); }   // staged word index
+template <int L> __device__ __forceinline__ uint32_t pwu(uint32_t i) { return i + 4u * (i / L); }
+template <int L> __device__ __forceinline__ int pe(int i) { return i + i / L; }         // exit-array index
+
 template <int NT, int L>
 struct TileSmem {
     static constexpr int T = NT * L;
     static constexpr int NW = NT / 32;
-    uint32_t w[(T + HALO) + (T + HALO) / 16 + 1];   // staged words, padded
-    uint32_t E[T + T / 16 + 1];                     // per position: first chain position past its segment
-    uint32_t wmap[NW][32];                          // per warp: exit for its 32 candidate entries
-    uint32_t warp_entry[NW];
+    static constexpr int TH = T + HALO;                 // staged words: the tile and its halo
+    static constexpr int WPAD = TH + 4 * (TH / L);      // 4 spare words per segment: conflict-free 16-byte reads
+    static constexpr int NE = T + T / L + 1;
+    uint4 w4[WPAD / 4];
+    uint16_t E[NE];                 // exact path: exit past each position's segment (relative); then the start list
+    uint32_t flt[257];              // per opcode: word counts a start may have (low 16 bits min, high max)
+    uint2 fd[257];                  // per opcode: fast operand form (id mask, flags, form; fixed words, capability)
+    uint8_t bnp[4][16];             // per bit-enum kind and mask: literal parameters of its known bits
+    uint32_t far[T / 32];           // successor marks two or more segments ahead
+    uint32_t sl_hi[NW];             // each warp's last segment's marks for the next warp's first segment
+    uint16_t X[NT];                 // guessed starts per segment
     uint16_t seg_entry[NT];
+    uint32_t wmap[NW][32];          // per warp: exit for its 32 candidate entries
+    uint32_t warp_entry[NW];
     uint32_t warp_tot[NW];
     // tile scalars
     long long tile;
-    int m;
-    uint32_t k, len_rel, tile_n, hdr;
     long long mod_base;
-    uint32_t entry, exitp;
+    int m;
+    uint32_t k, end_s, tile_n, hdr, ph;
+    uint32_t entry, exitp, exitX, cnt1, cnt2;
+    int need_exact;
+    int count_pub;                  // the row count is published already
     unsigned long long row_base;
     unsigned int count;
     int timeout;
@@ -230,16 +280,58 @@ struct TileSmem {
 };
 
 template <int NT, int L>
-__global__ void __launch_bounds__(NT) k_tile(Params P)
+__global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
 {
     using S = TileSmem<NT, L>;
     constexpr int T = S::T;
     constexpr int NW = S::NW;
+    constexpr int TH = S::TH;
     constexpr int WSPAN = 32 * L;                  // words per warp segment
+    constexpr uint32_t SEGM = (1u << L) - 1u;
+    constexpr uint32_t FULL = 0xffffffffu;
+    static_assert(L == 8 || L == 16, "segments of 8 or 16 words");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S &s = *reinterpret_cast<S *>(smem_raw);
+    uint32_t *ws = reinterpret_cast<uint32_t *>(s.w4);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int lo = tid * L;
     const spvt::Tables &TB = g_spv_tables;
+
+    // per-opcode tables, once per CTA
+    for (int o = tid; o < 257; o += NT) {
+        uint32_t f = 0xffffu;                      // min 0xffff, max 0: no word count fits
+        if (o < 256) {
+            const spvt::OpDesc &d = TB.ops[o];
+            if (d.flags & 1) {
+                uint32_t mn, mx = 0xffffu;
+                if (d.fast & 1) {
+                    const uint32_t need = 1u + d.nfixed, tail = (d.fast >> 1) & 7u;
+                    mn = need;
+                    if (tail == 0) mx = need;
+                    else if (tail == 4 && !(d.fast & 16)) mn = need + 1;
+                } else {
+                    mn = 1u + ((d.flags >> 1) & 1u) + ((d.flags >> 2) & 1u);
+                }
+                f = mn | (mx << 16);
+            }
+            s.fd[o] = make_uint2((uint32_t)d.id_mask | ((uint32_t)d.flags << 16) | ((uint32_t)d.fast << 24),
+                                 (uint32_t)d.nfixed | ((uint32_t)(uint8_t)d.cap << 8) | ((uint32_t)d.bkind << 16));
+        } else {
+            s.fd[o] = make_uint2(0u, 0u);          // opcodes past the table: unknown
+        }
+        s.flt[o] = f;
+    }
+    // a bit-enum word's parameters: its known bits all lie below bit 4
+    static_assert(spvt::NUM_BKINDS == 4, "bit-enum kinds");
+    for (int i = tid; i < 64; i += NT) {
+        const int kind = i >> 4, x = i & 15;
+        uint32_t np = 0;
+        for (int b = 0; b < 32; b++) {
+            const spvt::EnDesc &e = TB.benum[kind][b];
+            if (e.known && b < 4 && ((x >> b) & 1)) np += e.nparam;
+        }
+        s.bnp[kind][x] = (uint8_t)np;
+    }
 
     // a ticket is taken only when its tile starts: tiles wait on their
     // predecessors' published states, and a ticket held while its CTA works
@@ -251,75 +343,216 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             s.tile = g0;
             if (g0 < n_tiles) {
                 const TileRec r = P.tile_rec[g0];
-                s.m = (int)r.m; s.k = r.k; s.mod_base = r.base; s.hdr = r.hdr;
-                s.len_rel = r.len_rel;
+                s.m = (int)r.m; s.k = r.k; s.mod_base = r.base; s.hdr = r.hdr; s.ph = r.ph;
+                s.end_s = r.len_rel;
                 s.tile_n = r.len_rel < (uint32_t)T ? r.len_rel : (uint32_t)T;
                 s.timeout = 0;
                 s.err_key = NO_KEY;
                 s.n_cap = s.n_mm = s.n_ep = s.n_fn = 0;
                 s.decl_lo = s.decl_hi = s.req_lo = s.req_hi = 0;
                 s.max_rid = 0; s.flags = 0; s.n_ids = 0; s.vnext = 0;
+                s.cnt1 = 0; s.cnt2 = 0; s.exitX = DEAD; s.need_exact = 0; s.count_pub = 0;
             }
         }
+        for (int i = tid; i < T / 32; i += NT) s.far[i] = 0u;
         __syncthreads();
         const long long g = s.tile;
         if (g >= n_tiles) break;
-        const uint32_t len_rel = s.len_rel, tile_n = s.tile_n, k = s.k;
+        const uint32_t end_s = s.end_s, tile_n = s.tile_n, k = s.k, ph = s.ph;
         const int m = s.m;
         const bool live = (s.hdr == S_OK);
-        const uint32_t *src = P.words + s.mod_base + (long long)k * T;
+        const long long tbase = s.mod_base - (long long)ph + (long long)k * T;   // word index of tile-local 0
+        const uint32_t tb_rel = k * (uint32_t)T - ph;                         // its module position (k > 0)
+        const uint32_t *src = P.words + tbase;
+        const int lo_ok = k == 0 ? (int)ph : 0;                               // first module word of the tile
 
-        // 1. stage, with asynchronous copies (one round trip for the tile)
+        // 1. stage the tile and its halo with 16-byte asynchronous copies (one
+        //    round trip); the ragged ends of the module by smaller copies,
+        //    words outside the module as zeros
         {
-            int nload = (int)(len_rel < (uint32_t)(T + HALO) ? len_rel : (uint32_t)(T + HALO));
-            if (!live) nload = 0;
-            for (int i = tid; i < T + HALO; i += NT) {
-                if (i < nload) cp_async4(&s.w[pad(i)], src + i);
-                else s.w[pad(i)] = 0u;
+            const int e = (int)(end_s < (uint32_t)TH ? end_s : (uint32_t)TH);
+            for (int c = tid; c < TH / 4; c += NT) {
+                const int s0 = 4 * c;
+                uint32_t *dst = ws + pw<L>(s0);
+                if (s0 >= e) {
+                    *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+                } else if (s0 >= lo_ok) {
+                    cp_async16(dst, src + s0, (uint32_t)((e - s0 < 4 ? e - s0 : 4) * 4));
+                } else {
+                    #pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        if (s0 + q >= lo_ok && s0 + q < e) cp_async4(dst + q, src + s0 + q);
+                        else dst[q] = 0u;
+                    }
+                }
             }
             cp_async_wait_all();
         }
         __syncthreads();
-        auto word = [&](uint32_t p) -> uint32_t { return p < (uint32_t)(T + HALO) ? s.w[pad((int)p)] : __ldg(src + p); };
 
-        // 2a. per-segment exits (backwards dynamic programming)
-        {
-            int lo = tid * L;
-            int hi = lo + L;
-            if (hi > (int)tile_n) hi = (int)tile_n;
-            for (int q = hi - 1; q >= lo; q--) {
-                uint32_t wc = s.w[pad(q)] >> 16;
-                uint32_t e;
-                if (wc == 0 || (uint32_t)q + wc > len_rel) e = DEAD;
-                else if (q + (int)wc >= hi) e = (uint32_t)q + wc;
-                else e = s.E[pad(q + (int)wc)];
-                s.E[pad(q)] = e;
+        // 2. guessed starts of my segment, and where each one's successor lies;
+        //    my segment's words also go straight to the encoded output
+        uint32_t X = 0, sl = 0, ne = 0;
+        const int n_copy = (int)(end_s < (uint32_t)T ? end_s : (uint32_t)T);   // tile-local end of the module's words
+        if (live || (P.out && P.out_vec)) {
+            uint32_t wv[L];
+            #pragma unroll
+            for (int c = 0; c < L / 4; c++) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(ws + pw<L>(lo + 4 * c));
+                wv[4 * c] = v.x; wv[4 * c + 1] = v.y; wv[4 * c + 2] = v.z; wv[4 * c + 3] = v.w;
+            }
+            if (P.out && P.out_vec) {
+                // 5. encode: in the fused path every field an instruction writes back
+                // (first word from wc/op, result type, result id) is decoded from the
+                // staged words themselves, so the re-encoded tile is the staged tile;
+                // the header bound is patched by the finalize pass
+                uint32_t *dst = P.out + tbase;
+                #pragma unroll
+                for (int c = 0; c < L / 4; c++) {
+                    const int s0 = lo + 4 * c;
+                    if (s0 >= lo_ok && s0 + 4 <= n_copy) {
+                        *reinterpret_cast<uint4 *>(dst + s0) = make_uint4(wv[4 * c], wv[4 * c + 1], wv[4 * c + 2], wv[4 * c + 3]);
+                    } else if (s0 < n_copy && s0 + 4 > lo_ok) {
+                        #pragma unroll
+                        for (int q = 0; q < 4; q++)
+                            if (s0 + q >= lo_ok && s0 + q < n_copy) dst[s0 + q] = wv[4 * c + q];
+                    }
+                }
+            }
+            if (live) {
+                if (k == 0 && tid == 0) {              // the module header is never a start
+                    #pragma unroll
+                    for (int j = 0; j < 8; j++)
+                        if (j < (int)ph + 5) wv[j] = 0u;
+                }
+                const int lim = (int)tile_n - lo;      // a successor at or past lim leaves the tile
+                uint32_t ex = 0, farm = 0;
+                #pragma unroll
+                for (int j = 0; j < L; j++) {
+                    const uint32_t w = wv[j], wc = w >> 16, op = w & 0xffffu;
+                    const uint32_t f = s.flt[op < 256u ? op : 256u];
+                    const bool pl = wc >= (f & 0xffffu) && wc <= (f >> 16);
+                    const int nx = j + (int)wc;
+                    X |= pl ? (1u << j) : 0u;
+                    const bool leaves = pl && nx >= lim;
+                    ne += leaves ? 1u : 0u;
+                    ex = leaves ? (uint32_t)(lo + nx) : ex;
+                    sl |= (pl && nx < lim && nx < 2 * L) ? (1u << (nx & 31)) : 0u;
+                    farm |= (pl && nx < lim && nx >= 2 * L) ? (1u << j) : 0u;
+                }
+                while (farm) {                         // successors two or more segments ahead (long instructions)
+                    const int j = __ffs(farm) - 1;
+                    farm &= farm - 1;
+                    const int at = lo + j + (int)(ws[pw<L>(lo + j)] >> 16);
+                    atomicOr(&s.far[at >> 5], 1u << (at & 31));
+                }
+                s.X[tid] = (uint16_t)X;
+                if (lane == 31) s.sl_hi[wid] = sl;
+                if (ne) s.exitX = ex;                  // one writer when the guess is a chain
             }
         }
         __syncthreads();
-        // 2b. per warp: exits of the 32 candidate entries at the start of its segment
-        {
-            uint32_t wb = (uint32_t)wid * WSPAN;
-            uint32_t we = wb + WSPAN < tile_n ? wb + WSPAN : tile_n;
-            uint32_t x = wb + lane;
-            while (x < we) { x = s.E[pad((int)x)]; if (x == DEAD) break; }
-            s.wmap[wid][lane] = x;
+        // the guess is a chain when the successor marks are exactly the
+        // candidates but one (the first), each mark made once, and exactly
+        // one candidate leaves the tile
+        if (live) {
+            uint32_t prev = __shfl_up_sync(FULL, sl, 1);
+            if (lane == 0) prev = wid ? s.sl_hi[wid - 1] : 0u;
+            const uint32_t succ = (sl & SEGM) | (prev >> L) | ((s.far[lo >> 5] >> (lo & 31)) & SEGM);
+            uint32_t r1 = (uint32_t)__popc(X & ~succ) | ((uint32_t)__popc(succ & ~X) << 16);
+            uint32_t r2 = ne | ((uint32_t)__popc(X) << 16);
+            r1 = __reduce_add_sync(FULL, r1);
+            r2 = __reduce_add_sync(FULL, r2);
+            if (lane == 0) { atomicAdd(&s.cnt1, r1); atomicAdd(&s.cnt2, r2); }
         }
         __syncthreads();
-        // 2c. warp 0: tile map for entries 0..31, publish, look back for the entry
+        const uint32_t exitX = s.exitX;
+        bool fast = false;
+        {
+            const uint32_t c1 = s.cnt1, c2 = s.cnt2;
+            const uint32_t nA = c1 & 0xffffu, nB = c1 >> 16, nE = c2 & 0xffffu, nX = c2 >> 16;
+            fast = live && (nX == 0 || (nA == 1 && nB == 0 && nE == 1 && exitX <= end_s));
+        }
+
+        // exact path: per-position exits of each segment (backward pass),
+        // then per warp the exits of its 32 candidate entries
+        auto Eabs = [&](uint32_t x) -> uint32_t {   // x < tile_n
+            const uint32_t e = s.E[pe<L>((int)x)];
+            if (e == 0xffffu) return DEAD;
+            const uint32_t seg_hi = (x / L + 1) * L;
+            return (seg_hi < tile_n ? seg_hi : tile_n) + e;
+        };
+        auto exact_maps = [&]() {
+            {
+                const int hi = lo + L < (int)tile_n ? lo + L : (int)tile_n;
+                for (int q = hi - 1; q >= lo; q--) {
+                    const uint32_t wc = ws[pw<L>(q)] >> 16;
+                    uint32_t e;
+                    if (wc == 0 || (uint32_t)q + wc > end_s) e = 0xffffu;
+                    else if (q + (int)wc >= hi) e = (uint32_t)(q + (int)wc - hi);
+                    else e = s.E[pe<L>(q + (int)wc)];
+                    s.E[pe<L>(q)] = (uint16_t)e;
+                }
+            }
+            __syncthreads();
+            {
+                const uint32_t wb = (uint32_t)wid * WSPAN;
+                const uint32_t we = wb + WSPAN < tile_n ? wb + WSPAN : tile_n;
+                uint32_t x = wb + lane;
+                while (x < we) { x = Eabs(x); if (x == DEAD) break; }
+                s.wmap[wid][lane] = x;
+            }
+            __syncthreads();
+        };
+        // exact path: from the tile entry e through the warp maps; the warps'
+        // entries and the tile's exit (lane 0 of warp 0)
+        auto exact_compose = [&](uint32_t x0) {
+            uint32_t xw = x0;
+            for (int w2 = 0; w2 < NW; w2++) {
+                const uint32_t wb = (uint32_t)w2 * WSPAN;
+                const uint32_t we = wb + WSPAN < tile_n ? wb + WSPAN : tile_n;
+                if (xw == DEAD || xw >= tile_n || xw >= we) { s.warp_entry[w2] = DEAD; continue; }
+                s.warp_entry[w2] = xw;
+                if (xw - wb < 32) xw = s.wmap[w2][xw - wb];
+                else { while (xw < we) { xw = Eabs(xw); if (xw == DEAD) break; } }
+            }
+            return xw;
+        };
+        if (live && !fast) exact_maps();
+
+        // 3. warp 0: the tile map for entries 0..31, published; the look-back
+        //    for the tile's entry; the tile's exit, published. Meanwhile the
+        //    other warps encode.
         if (wid == 0) {
-            uint32_t x = s.wmap[0][lane];
-            for (int w2 = 1; w2 < NW; w2++) {
-                if (x == DEAD || x >= tile_n) break;
-                uint32_t wb = (uint32_t)w2 * WSPAN;
-                if (x - wb < 32) x = s.wmap[w2][x - wb];
-                else if (x < wb + WSPAN) { x = UNRES; break; }
+            uint32_t x;
+            if (fast) {
+                // a candidate entry on the guessed chain leaves with it; any
+                // other is followed a few steps until it joins the chain,
+                // dies or leaves the tile (else the map cannot tell)
+                uint32_t pos = (uint32_t)lane;
+                x = UNRES;
+                #pragma unroll 1
+                for (int st = 0; st < 4; st++) {
+                    if (pos >= tile_n) { x = pos; break; }
+                    if ((s.X[pos / L] >> (pos % L)) & 1u) { x = exitX; break; }
+                    const uint32_t wc = ws[pw<L>((int)pos)] >> 16;
+                    if (wc == 0 || pos + wc > end_s) { x = DEAD; break; }
+                    pos += wc;
+                }
+            } else {
+                x = s.wmap[0][lane];
+                for (int w2 = 1; w2 < NW; w2++) {
+                    if (x == DEAD || x >= tile_n) break;
+                    const uint32_t wb = (uint32_t)w2 * WSPAN;
+                    if (x - wb < 32) x = s.wmap[w2][x - wb];
+                    else if (x < wb + WSPAN) { x = UNRES; break; }
+                }
             }
-            uint32_t mv = (x == DEAD || x == UNRES) ? x : x + k * (uint32_t)T;
-            long long first = g - (long long)k;
+            const uint32_t mv = (x == DEAD || x == UNRES) ? x : x + tb_rel;
+            const long long first = g - (long long)k;
             const bool stalled = (g == P.stall_tile);
             const bool map_only = (g == P.stall_map_tile);
-            bool need_lookback = live && k > 0;
+            const bool need_lookback = live && k > 0;
             if (need_lookback && !stalled) {
                 // a map entry of a tile after a module's first is never 0 (an
                 // exit lies past the tile's start, DEAD and UNRES are not 0),
@@ -327,13 +560,16 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                 // ordering against the MAP state, which only tells the
                 // look-back that the map is on its way
                 if (!map_only) st_relaxed32(&P.tmap[g * NCAND + lane], mv);
+                const bool inline_map = fast && !map_only && exitX != DEAD;
+                const uint32_t cm = __ballot_sync(FULL, inline_map && x == exitX);
                 __syncwarp();
-                if (lane == 0) st_relaxed(&P.tstate[g], F_MAP);
+                if (lane == 0)
+                    st_relaxed(&P.tstate[g], inline_map ? (F_FMAP | ((unsigned long long)exitX << 32) | cm) : F_MAP);
             }
-            // entry of this tile (module-relative)
+            // entry of this tile (tile-local)
             uint32_t entry;
             if (!live) entry = DEAD;
-            else if (k == 0) entry = 5;
+            else if (k == 0) entry = ph + 5;
             else {
                 // find the nearest predecessor with a published exit
                 long long hi_j = g - 1;
@@ -341,12 +577,14 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                 long long anchor = -1;
                 uint32_t ax = DEAD;
                 bool gave_up = false;
+                unsigned long long st_last = 0;
                 for (;;) {
                     long long j = hi_j - lane;
                     unsigned long long st = j >= first ? ld_relaxed(&P.tstate[j]) : F_EXIT;
+                    st_last = st;
                     unsigned long long f = st & F_MASK;
-                    unsigned exitm = __ballot_sync(0xffffffffu, j < first || f == F_EXIT);
-                    unsigned nonem = __ballot_sync(0xffffffffu, j >= first && f == 0);
+                    unsigned exitm = __ballot_sync(FULL, j < first || f == F_EXIT);
+                    unsigned nonem = __ballot_sync(FULL, j >= first && f == 0);
                     if (exitm) {
                         int le = __ffs(exitm) - 1;
                         if (nonem & ((1u << le) - 1u)) {
@@ -354,7 +592,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                             spin_pause();
                             continue;
                         }
-                        unsigned long long sv = __shfl_sync(0xffffffffu, st, le);
+                        unsigned long long sv = __shfl_sync(FULL, st, le);
                         anchor = hi_j - le;
                         ax = anchor < first ? 5u : (uint32_t)(sv & 0xffffffffu);
                         break;
@@ -366,25 +604,30 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                     }
                     hi_j -= 32;
                 }
-                // apply predecessors' maps from the anchor forward; an entry
-                // read as 0 is not visible yet and is read again
+                // apply predecessors' maps from the anchor forward. When every
+                // tile between the anchor and this one was read in the last poll
+                // (one per lane), an inline map settles a marked entry without
+                // a map entry; otherwise the map entry is read (one read as 0 is
+                // not visible yet and is read again)
                 uint32_t xx = ax;
-                for (long long t = anchor + 1; t < g && !gave_up; t += 8) {
-                    uint32_t mrow[8];
-                    #pragma unroll
-                    for (int q = 0; q < 8; q++) mrow[q] = (t + q < g) ? ld_relaxed32(&P.tmap[(t + q) * NCAND + lane]) : 0u;
-                    #pragma unroll
-                    for (int q = 0; q < 8; q++) {
-                        long long tt = t + q;
-                        if (tt >= g) break;
+                const bool in_regs = (hi_j == g - 1);
+                for (long long tt = anchor + 1; tt < g && !gave_up; tt++) {
+                    {
                         uint32_t kt = (uint32_t)(tt - first);
-                        uint32_t tb = kt * (uint32_t)T;
-                        uint32_t val = __shfl_sync(0xffffffffu, mrow[q], (int)((xx - tb) & 31u));
+                        uint32_t tb = kt * (uint32_t)T - ph;
                         if (xx == DEAD || xx >= tb + (uint32_t)T) continue;
+                        if (in_regs) {
+                            const unsigned long long stt = __shfl_sync(FULL, st_last, (int)(hi_j - tt));
+                            if ((stt & F_MASK) == F_FMAP && xx - tb < 32 && ((stt >> (xx - tb)) & 1ull)) {
+                                xx = tb + (uint32_t)((stt >> 32) & 0x3ffffu);
+                                continue;
+                            }
+                        }
+                        uint32_t val = xx - tb < 32 ? __shfl_sync(FULL, ld_relaxed32(&P.tmap[tt * NCAND + lane]), (int)((xx - tb) & 31u)) : 0u;
                         while (xx - tb < 32 && val == 0u) {
                             if (++spins > P.max_spins) { gave_up = true; break; }
                             spin_pause();
-                            val = __shfl_sync(0xffffffffu, ld_relaxed32(&P.tmap[tt * NCAND + lane]), (int)((xx - tb) & 31u));
+                            val = __shfl_sync(FULL, ld_relaxed32(&P.tmap[tt * NCAND + lane]), (int)((xx - tb) & 31u));
                         }
                         if (gave_up) break;
                         if (xx - tb < 32 && val != UNRES) { xx = val; continue; }
@@ -393,7 +636,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                         for (;;) {
                             st = 0;
                             if (lane == 0) st = ld_relaxed(&P.tstate[tt]);
-                            st = __shfl_sync(0xffffffffu, st, 0);
+                            st = __shfl_sync(FULL, st, 0);
                             if ((st & F_MASK) == F_EXIT) break;
                             if (++spins > P.max_spins) { gave_up = true; break; }
                             spin_pause();
@@ -402,68 +645,101 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                         xx = (uint32_t)(st & 0xffffffffu);
                     }
                 }
-                entry = gave_up ? DEAD : xx;
+                entry = gave_up ? DEAD : (xx == DEAD ? DEAD : xx - tb_rel);
                 if (gave_up && lane == 0) s.timeout = 1;
             }
-            // 2d. compose through the warp segments for the true entry
             if (lane == 0) {
-                uint32_t x0 = (entry == DEAD) ? DEAD : (entry >= k * (uint32_t)T ? entry - k * (uint32_t)T : DEAD);
-                uint32_t xw = x0;
-                for (int w2 = 0; w2 < NW; w2++) {
-                    uint32_t wb = (uint32_t)w2 * WSPAN;
-                    uint32_t we = wb + WSPAN < tile_n ? wb + WSPAN : tile_n;
-                    if (xw == DEAD || xw >= tile_n || xw >= we) { s.warp_entry[w2] = DEAD; continue; }
-                    s.warp_entry[w2] = xw;
-                    if (xw - wb < 32) xw = s.wmap[w2][xw - wb];
-                    else { while (xw < we) { xw = s.E[pad((int)xw)]; if (xw == DEAD) break; } }
+                uint32_t xw = DEAD;
+                bool known_exit = true;
+                if (!live || entry == DEAD) xw = DEAD;
+                else if (fast) {
+                    if (entry >= tile_n) xw = entry;
+                    else if ((s.X[entry / L] >> (entry % L)) & 1u) xw = exitX;
+                    else { known_exit = false; s.need_exact = 1; }     // the entry is not on the guessed chain
+                } else {
+                    xw = exact_compose(entry);
                 }
-                s.entry = x0;
+                s.entry = entry;
                 s.exitp = xw;
-                if (live && g != P.stall_tile && g != P.stall_map_tile) {
-                    uint32_t mx = xw == DEAD ? DEAD : xw + k * (uint32_t)T;
+                if (known_exit && live && g != P.stall_tile && g != P.stall_map_tile) {
+                    const uint32_t mx = xw == DEAD ? DEAD : xw + tb_rel;
                     st_relaxed(&P.tstate[g], F_EXIT | (unsigned long long)mx);
                 }
             }
-        } else if (P.out) {
-            // 5. encode, by the other warps while warp 0 looks back. In the
-            // fused path every field an instruction writes back (first word
-            // from wc/op, result type, result id) is decoded from the staged
-            // words themselves, so the re-encoded tile is the staged tile; the
-            // header bound is patched by the finalize pass.
-            uint32_t *dst = P.out + s.mod_base + (long long)k * T;
-            int n = live ? (int)tile_n : (int)(len_rel < (uint32_t)T ? len_rel : (uint32_t)T);
-            if (live) {
-                for (int i = tid - 32; i < n; i += NT - 32) dst[i] = s.w[pad(i)];
-            } else {
-                for (int i = tid - 32; i < n; i += NT - 32) dst[i] = __ldg(src + i);
+            __syncwarp();
+            // the tile's row count, published as soon as its entry is known: the
+            // guessed chain's starts from the entry on (none without a live
+            // entry). Every later tile's first row waits on this count.
+            if (!live || entry == DEAD || (fast && s.need_exact == 0)) {
+                uint32_t c = 0;
+                if (live && entry != DEAD && entry < tile_n) {
+                    for (int t = lane; t < NT; t += 32) {
+                        const uint32_t lo_t = (uint32_t)t * L;
+                        uint32_t x = s.X[t];
+                        if (lo_t + L <= entry) x = 0;
+                        else if (lo_t < entry) x &= ~((1u << (entry - lo_t)) - 1u);
+                        c += (uint32_t)__popc(x);
+                    }
+                }
+                c = __reduce_add_sync(FULL, c);
+                if (lane == 0) {
+                    s.count_pub = 1;
+                    if (g != P.stall_tile && g != P.stall_map_tile)
+                        st_relaxed(&P.cstate[g], (g == 0 ? F_EXIT : F_MAP) | c);
+                }
             }
+        } else if (P.out && !P.out_vec) {
+            // encode word by word when the output buffer's 16-byte phase is not
+            // the words' (the other warps, while warp 0 looks back)
+            uint32_t *dst = P.out + tbase;
+            for (int i = tid - 32 + lo_ok; i < n_copy; i += NT - 32) dst[i] = ws[pw<L>(i)];
         }
         __syncthreads();
-        // 2e. per warp: entry of each 16-word segment (serial walk by lane 0)
-        s.seg_entry[tid] = NONE16;
-        __syncwarp();
-        if (lane == 0) {
-            uint32_t x = s.warp_entry[wid];
-            uint32_t wb = (uint32_t)wid * WSPAN;
-            uint32_t we = wb + WSPAN < tile_n ? wb + WSPAN : tile_n;
-            while (x != DEAD && x < we) {
-                s.seg_entry[x / L] = (uint16_t)x;
-                x = s.E[pad((int)x)];
+        // the entry missed the guessed chain: the exact path for this tile's starts
+        const bool need_exact = s.need_exact != 0;
+        if (need_exact) {
+            exact_maps();
+            if (tid == 0) {
+                const uint32_t xw = exact_compose(s.entry);
+                s.exitp = xw;
+                if (g != P.stall_tile && g != P.stall_map_tile) {
+                    const uint32_t mx = xw == DEAD ? DEAD : xw + tb_rel;
+                    st_relaxed(&P.tstate[g], F_EXIT | (unsigned long long)mx);
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();
-        // 3. mark starts in my segment; detect the framing error if the chain dies here
+        // 4. my segment's starts; the framing error if the chain dies here
         uint32_t mask = 0;
         int ferr = -1;          // 0 zero word count, 1 truncated
-        {
-            int lo = tid * L;
-            int hi = lo + L < (int)tile_n ? lo + L : (int)tile_n;
+        if (fast && !need_exact) {
+            const uint32_t e = s.entry;
+            if (e != DEAD && e < tile_n) {
+                if (e <= (uint32_t)lo) mask = X;
+                else if (e < (uint32_t)(lo + L)) mask = X & ~((1u << (e - (uint32_t)lo)) - 1u);
+            }
+        } else if (live) {
+            // per warp: entry of each segment (serial walk by lane 0), then the
+            // starts of my segment
+            s.seg_entry[tid] = NONE16;
+            __syncwarp();
+            if (lane == 0) {
+                uint32_t x = s.warp_entry[wid];
+                uint32_t wb = (uint32_t)wid * WSPAN;
+                uint32_t we = wb + WSPAN < tile_n ? wb + WSPAN : tile_n;
+                while (x != DEAD && x < we) {
+                    s.seg_entry[x / L] = (uint16_t)x;
+                    x = Eabs(x);
+                }
+            }
+            __syncwarp();
+            const int hi = lo + L < (int)tile_n ? lo + L : (int)tile_n;
             uint32_t p = s.seg_entry[tid];
             if (p != NONE16) {
                 while ((int)p < hi) {
-                    uint32_t wc = s.w[pad((int)p)] >> 16;
+                    uint32_t wc = ws[pw<L>((int)p)] >> 16;
                     if (wc == 0) { ferr = 0; break; }
-                    if (p + wc > len_rel) { ferr = 1; break; }
+                    if (p + wc > end_s) { ferr = 1; break; }
                     mask |= 1u << (p - lo);
                     p += wc;
                 }
@@ -472,19 +748,19 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
         const unsigned cnt = __popc(mask);
         unsigned incl = cnt;
         #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) { unsigned v = __shfl_up_sync(0xffffffffu, incl, d); if (lane >= d) incl += v; }
+        for (int d = 1; d < 32; d <<= 1) { unsigned v = __shfl_up_sync(FULL, incl, d); if (lane >= d) incl += v; }
         if (lane == 31) s.warp_tot[wid] = incl;
         __syncthreads();
         const bool stalled = (g == P.stall_tile || g == P.stall_map_tile);
         if (wid == 0) {                          // block scan of the warp counts; publish the tile's count
             unsigned v = lane < NW ? s.warp_tot[lane] : 0;
             #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) { unsigned u = __shfl_up_sync(0xffffffffu, v, d); if (lane >= d) v += u; }
+            for (int d = 1; d < 32; d <<= 1) { unsigned u = __shfl_up_sync(FULL, v, d); if (lane >= d) v += u; }
             if (lane < NW) s.warp_tot[lane] = v;
-            unsigned total = __shfl_sync(0xffffffffu, v, NW - 1);
+            unsigned total = __shfl_sync(FULL, v, NW - 1);
             if (lane == 0) {
                 s.count = total;
-                if (!stalled) st_relaxed(&P.cstate[g], (g == 0 ? F_EXIT : F_MAP) | total);
+                if (!stalled && !s.count_pub) st_relaxed(&P.cstate[g], (g == 0 ? F_EXIT : F_MAP) | total);
             }
         }
         __syncthreads();
@@ -492,17 +768,17 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
         const unsigned my_off = (wid ? s.warp_tot[wid - 1] : 0) + incl - cnt;
         // error keys hold tile-local rows until the flush adds the tile's first row
         if (ferr >= 0 && live) atomicMin(&s.err_key, make_key(my_off + cnt, R_FRAME, (uint32_t)ferr));
-        // 4. start list (reuses E)
-        uint16_t *S16 = reinterpret_cast<uint16_t *>(s.E);
+        // start list (reuses E)
+        uint16_t *S16 = s.E;
         {
             uint32_t x = mask;
             unsigned o = my_off;
-            while (x) { int b = __ffs(x) - 1; x &= x - 1; S16[o++] = (uint16_t)(tid * L + b); }
+            while (x) { int b = __ffs(x) - 1; x &= x - 1; S16[o++] = (uint16_t)(lo + b); }
         }
         __syncthreads();
-        // 4a. warp 0: the tile's first row (decoupled look-back over all tiles'
-        //     counts); meanwhile the other warps validate the tile's rows,
-        //     which needs no global row index, and warp 0 joins them after
+        // warp 0: the tile's first row (decoupled look-back over all tiles'
+        // counts); meanwhile the other warps validate the tile's rows, which
+        // needs no global row index, and warp 0 joins them after
         if (wid == 0) {
             unsigned long long excl = 0;
             if (g > 0) {
@@ -513,10 +789,10 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                     long long j = hi_j - lane;
                     unsigned long long st = j >= 0 ? ld_relaxed(&P.cstate[j]) : F_EXIT;
                     unsigned long long f = st & F_MASK;
-                    unsigned exitm = __ballot_sync(0xffffffffu, f == F_EXIT);
-                    unsigned nonem = __ballot_sync(0xffffffffu, f == 0);
+                    unsigned exitm = __ballot_sync(FULL, f == F_EXIT);
+                    unsigned nonem = __ballot_sync(FULL, f == 0);
                     int le = exitm ? __ffs(exitm) - 1 : 32;
-                    unsigned below = le == 32 ? 0xffffffffu : ((1u << le) - 1u);
+                    unsigned below = le == 32 ? FULL : ((1u << le) - 1u);
                     if (nonem & below) {
                         if (++spins > P.max_spins) { gave_up = true; break; }
                         spin_pause();
@@ -524,7 +800,7 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                     }
                     unsigned long long v = (lane <= le && j >= 0) ? (st & ~F_MASK) : 0ull;
                     #pragma unroll
-                    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+                    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
                     excl += v;
                     if (exitm) break;
                     hi_j -= 32;
@@ -538,68 +814,111 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
                 if (g == n_tiles - 1) P.ctrl->total_rows = excl + tile_count;
             }
         }
+        const uint32_t bound = P.ms[m].bound;
+        const long long arena_off = P.ms[m].arena_off;
+        const uint32_t id_slots = P.ms[m].id_slots;
         if (P.validate) {
             // rows in chunks of 32 from a shared counter: warp 0 joins when
-            // its look-back is done, and a slow chunk holds back no warp's
-            // later rows
-            const uint32_t bound = P.ms[m].bound;
-            const long long arena_off = P.ms[m].arena_off;
-            const uint32_t id_slots = P.ms[m].id_slots;
+            // its look-back is done. A row in the fast operand form (fixed ids
+            // and literals, then a plain tail or one bit-enum word; wholly in
+            // the tile, at most 32 words) is checked here, in the order of
+            // section 3.4.5's checks: known opcode, its word count against the
+            // form, every id operand in [1, bound); then its result id goes
+            // into the module's id set and the opcode's capability into the
+            // tile's requirements. Any other row takes the full operand walk.
             for (;;) {
                 unsigned rb = 0;
                 if (lane == 0) rb = atomicAdd(&s.vnext, 32u);
-                rb = __shfl_sync(0xffffffffu, rb, 0);
+                rb = __shfl_sync(FULL, rb, 0);
                 if (rb >= tile_count) break;
                 const unsigned r = rb + (unsigned)lane;
-                uint32_t ri = 0;
-                uint64_t req = 0;
-                uint32_t inserted = 0;
-                if (r < tile_count) {
-                    uint32_t p = S16[r];
-                    uint32_t w0 = s.w[pad((int)p)];           // staged: p lies in the tile
-                    uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
-                    const spvt::OpDesc &d = TB.ops[op < 256 ? op : 0];
-                    bool known = op < 256 && (d.flags & 1);
-                    if (known && (d.flags & 4)) {
-                        uint32_t q = (d.flags & 2) ? 2u : 1u;
-                        if (q < wc) ri = s.w[pad((int)(p + q))]; // within the halo
+                const bool have = r < tile_count;
+                const uint32_t p = have ? (uint32_t)S16[r] : 0u;
+                const uint32_t w0 = ws[pwu<L>(p)];
+                const uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
+                const uint2 fdv = s.fd[op < 256u ? op : 256u];
+                const uint32_t flags = (fdv.x >> 16) & 0xffu, form = fdv.x >> 24;
+                const uint32_t need = 1u + (fdv.y & 0xffu), tail = (form >> 1) & 7u;
+                const bool known = have && (flags & 1u);
+                const bool fastrow = known && (form & 1u) && !(flags & 8u) && p + wc <= (uint32_t)T && wc <= 32u;
+                // a bit-enum tail's word, staged: p < T and need <= 16
+                const uint32_t np = s.bnp[(fdv.y >> 16) & 3u][ws[pwu<L>(p + need)] & 15u];
+                bool ok;
+                if (tail == 0) ok = wc == need;
+                else if (tail == 4) ok = wc == need ? (form & 16u) != 0 : wc == need + 1u + np;
+                else ok = wc >= need && (tail != 3 || ((wc - need) & 1u) == 0);
+                ok = ok && fastrow;
+                uint32_t idm = ok ? (fdv.x & 0xffffu) : 0u;
+                if (ok && (tail == 1 || tail == 3))
+                    idm |= (wc == 32u ? FULL : ((1u << wc) - 1u)) & ~((1u << need) - 1u);
+                bool oob = false;
+                while (idm) {
+                    const uint32_t i = (uint32_t)(__ffs(idm) - 1);
+                    idm &= idm - 1;
+                    oob |= ws[pwu<L>(p + i)] - 1u >= bound - 1u;
+                }
+                if ((have && !known) || (fastrow && !ok) || oob)
+                    atomicMin(&s.err_key, make_key(r, !known ? R_UNKNOWN : (!ok ? R_BADOP : R_OOB), 0));
+                const bool good = ok && !oob;
+                uint32_t req_lo = 0, req_hi = 0, inserted = 0;
+                const int cap = (int)(int8_t)((fdv.y >> 8) & 0xffu);
+                if (good && cap >= 0) { if (cap < 32) req_lo = 1u << cap; else req_hi = 1u << (cap - 32); }
+                if (good && (flags & 4u) && arena_off >= 0) {
+                    const uint32_t ri = ws[pwu<L>(p + ((flags & 2u) ? 2u : 1u))];
+                    if (id_slots == 0) {
+                        // no wait on the old value: duplicates show up later as
+                        // fewer bits set than ids inserted
+                        atomicOr(&P.arena[arena_off + (ri >> 5)], 1u << (ri & 31));
+                        inserted = 1;
+                    } else if (idset_insert(P.arena + arena_off, id_slots, ri)) {
+                        atomicOr(&s.flags, MF_DUP);
+                    }
+                }
+                // the rest: the full operand walk (forms with strings, value
+                // enums and their parameters; rows that validation counts or
+                // measures; rows reaching past the tile or longer than 32 words)
+                if (__any_sync(FULL, known && !fastrow) && known && !fastrow) {
+                    const spvt::OpDesc &d = TB.ops[op];          // a known opcode (< 256)
+                    auto iw = [&](uint32_t q) -> uint32_t {
+                        const uint32_t a = p + q;
+                        return a < (uint32_t)TH ? ws[pwu<L>(a)] : __ldg(src + a);
+                    };
+                    auto sw = [&](uint32_t q) -> uint32_t { return ws[pwu<L>(p + q)]; };
+                    uint32_t ri = 0;
+                    if (d.flags & 4) {
+                        const uint32_t q = (d.flags & 2) ? 2u : 1u;
+                        if (q < wc) ri = sw(q);
                     }
                     if (d.flags & 8) {            // the few opcodes validation counts or measures
-                        if (op == 17) { atomicAdd(&s.n_cap, 1u); if (wc >= 2) { uint32_t c = word(p + 1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); } }
+                        if (op == 17) { atomicAdd(&s.n_cap, 1u); if (wc >= 2) { uint32_t c = iw(1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); } }
                         else if (op == 14) atomicAdd(&s.n_mm, 1u);
                         else if (op == 15) atomicAdd(&s.n_ep, 1u);
                         else if (op == 54) atomicAdd(&s.n_fn, 1u);
                     }
-                    if (!known) { atomicMin(&s.err_key, make_key(r, R_UNKNOWN, 0)); }
+                    // an instruction wholly inside the staged words (almost every one)
+                    // reads them without the per-word range check
+                    const Walk wk = p + wc <= (uint32_t)TH ? walk_instruction(sw, wc, d, bound)
+                                                           : walk_instruction(iw, wc, d, bound);
+                    if (!wk.ok) atomicMin(&s.err_key, make_key(r, R_BADOP, 0));
+                    else if (wk.oob) atomicMin(&s.err_key, make_key(r, R_OOB, 0));
                     else {
-                        auto iw = [&](uint32_t i) -> uint32_t { return word(p + i); };
-                        // an instruction wholly inside the staged words (almost every one) reads
-                        // them without the per-word range check
-                        auto sw = [&](uint32_t i) -> uint32_t { return s.w[pad((int)(p + i))]; };
-                        Walk wk = p + wc <= (uint32_t)(T + HALO) ? walk_instruction(sw, wc, d, bound)
-                                                                  : walk_instruction(iw, wc, d, bound);
-                        if (!wk.ok) atomicMin(&s.err_key, make_key(r, R_BADOP, 0));
-                        else if (wk.oob) atomicMin(&s.err_key, make_key(r, R_OOB, 0));
-                        else {
-                            if ((d.flags & 4) && arena_off >= 0) {
-                                if (id_slots == 0) {
-                                    // no wait on the old value: duplicates show up later as
-                                    // fewer bits set than ids inserted
-                                    atomicOr(&P.arena[arena_off + (ri >> 5)], 1u << (ri & 31));
-                                    inserted = 1;
-                                } else if (idset_insert(P.arena + arena_off, id_slots, ri)) {
-                                    atomicOr(&s.flags, MF_DUP);
-                                }
+                        if ((d.flags & 4) && arena_off >= 0) {
+                            if (id_slots == 0) {
+                                atomicOr(&P.arena[arena_off + (ri >> 5)], 1u << (ri & 31));
+                                inserted = 1;
+                            } else if (idset_insert(P.arena + arena_off, id_slots, ri)) {
+                                atomicOr(&s.flags, MF_DUP);
                             }
-                            req = wk.req;
-                            if (d.flags & 8) req |= width_caps(iw, op, wc);
                         }
+                        uint64_t req = wk.req;
+                        if (d.flags & 8) req |= width_caps(iw, op, wc);
+                        req_lo = (uint32_t)req;
+                        req_hi = (uint32_t)(req >> 32);
                     }
                 }
-                // warp-level aggregation, then one shared atomic per warp
-                uint32_t rlo = __reduce_or_sync(0xffffffffu, (uint32_t)req);
-                uint32_t rhi = __reduce_or_sync(0xffffffffu, (uint32_t)(req >> 32));
-                uint32_t nins = __reduce_add_sync(0xffffffffu, inserted);
+                const uint32_t rlo = __reduce_or_sync(FULL, req_lo);
+                const uint32_t rhi = __reduce_or_sync(FULL, req_hi);
+                const uint32_t nins = __reduce_add_sync(FULL, inserted);
                 if (lane == 0) {
                     if (rlo) atomicOr(&s.req_lo, rlo);
                     if (rhi) atomicOr(&s.req_hi, rhi);
@@ -608,35 +927,37 @@ __global__ void __launch_bounds__(NT) k_tile(Params P)
             }
         }
         __syncthreads();
-        // 4b. the table rows, at the tile's first row; the largest result id
+        // the table rows, at the tile's first row (each warp its chunks of 32
+        // rows); the largest result id
         const unsigned long long row_base = s.row_base;
-        for (unsigned rb = 0; rb < tile_count; rb += NT) {
-            const unsigned r = rb + tid;
-            uint32_t ri = 0;
-            if (r < tile_count) {
-                // a start lies in the tile and the result type and id within two
-                // words of it, inside the 64-word halo: staged, read directly
-                uint32_t p = S16[r];
-                uint32_t w0 = s.w[pad((int)p)];
-                uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
-                const spvt::OpDesc &d = TB.ops[op < 256 ? op : 0];
-                uint32_t rt = 0;
-                if (op < 256 && (d.flags & 1)) {
-                    uint32_t q = 1;
-                    if (d.flags & 2) { if (q < wc) rt = s.w[pad((int)(p + q))]; q++; }
-                    if (d.flags & 4) { if (q < wc) ri = s.w[pad((int)(p + q))]; }
-                }
-                unsigned long long row = row_base + r;
-                if ((long long)row < P.cap_rows) {
-                    P.op[row] = (uint16_t)op; P.wc[row] = (uint16_t)wc;
-                    P.off[row] = (uint64_t)(s.mod_base + (long long)k * T + p);
-                    P.rtype[row] = rt; P.rid[row] = ri; P.mod[row] = (uint32_t)m;
-                } else {
-                    atomicOr(&s.flags, MF_CAPACITY);
+        {
+            uint32_t rmax = 0;
+            for (unsigned rb = 32u * (unsigned)wid; rb < tile_count; rb += NT) {
+                const unsigned r = rb + (unsigned)lane;
+                if (r < tile_count) {
+                    // a start lies in the tile and the result type and id within two
+                    // words of it, inside the 64-word halo: staged, read directly
+                    const uint32_t p = S16[r];
+                    const uint32_t w0 = ws[pwu<L>(p)];
+                    const uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
+                    const uint32_t flags = (s.fd[op < 256u ? op : 256u].x >> 16) & 0xffu;
+                    const uint32_t w1 = ws[pwu<L>(p + 1)], w2 = ws[pwu<L>(p + 2)];
+                    uint32_t rt = 0, ri = 0;
+                    if (flags & 2u) { if (wc > 1) rt = w1; if ((flags & 4u) && wc > 2) ri = w2; }
+                    else if ((flags & 4u) && wc > 1) ri = w1;
+                    rmax = ri > rmax ? ri : rmax;
+                    const unsigned long long row = row_base + r;
+                    if ((long long)row < P.cap_rows) {
+                        P.op[row] = (uint16_t)op; P.wc[row] = (uint16_t)wc;
+                        P.off[row] = (uint64_t)(tbase + p);
+                        P.rtype[row] = rt; P.rid[row] = ri; P.mod[row] = (uint32_t)m;
+                    } else {
+                        atomicOr(&s.flags, MF_CAPACITY);
+                    }
                 }
             }
-            uint32_t mx = __reduce_max_sync(0xffffffffu, ri);
-            if (lane == 0 && mx) atomicMax(&s.max_rid, mx);
+            rmax = __reduce_max_sync(FULL, rmax);
+            if (lane == 0 && rmax) atomicMax(&s.max_rid, rmax);
         }
         __syncthreads();
         // 6. flush the tile's aggregates to the module
@@ -972,7 +1293,9 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 Layout make_layout(int n_mod, long long n_words, long long arena_words, int tile_words)
 {
     Layout L{};
-    L.max_tiles = n_words / tile_words + n_mod + 1;
+    // a module of len words (first word ph < 4 past a 16-byte boundary) has
+    // ceil((len + ph) / T) tiles, at least one: at most (len + T + 2) / T
+    L.max_tiles = (n_words + 2LL * n_mod) / tile_words + n_mod + 1;
     L.arena_words = arena_words > 0 ? arena_words : 2 * n_words + 64LL * n_mod + 64;
     size_t o = 0;
     L.ctrl = o; o = al(o + sizeof(Ctrl));
@@ -1010,10 +1333,11 @@ int resolve_cfg(const spv_config *c, Cfg *out, int n_modules, long long n_words)
         if (c->test_stall_tile > 0) r.stall_tile = c->test_stall_tile - 1;
         if (c->test_stall_tile < 0) r.stall_map_tile = -c->test_stall_tile - 1;
     }
-    if (r.NT != 128 && r.NT != 256 && r.NT != 512) return SPV_E_ARG;
+    if (r.NT != 64 && r.NT != 128 && r.NT != 256 && r.NT != 512) return SPV_E_ARG;
     if (r.T % r.NT) return SPV_E_ARG;
     r.L = r.T / r.NT;
     if (r.L != 8 && r.L != 16) return SPV_E_ARG;
+    if ((r.NT == 512 && r.L != 16) || (r.NT == 64 && r.L != 8)) return SPV_E_ARG;
     *out = r;
     return 0;
 }
@@ -1056,6 +1380,7 @@ int dispatch_tile(const Params &P, const Cfg &c, int grid, cudaStream_t st)
     if (c.NT == 256 && c.L == 8) return launch_tile_kernel<256, 8>(P, grid, st);
     if (c.NT == 128 && c.L == 16) return launch_tile_kernel<128, 16>(P, grid, st);
     if (c.NT == 128 && c.L == 8) return launch_tile_kernel<128, 8>(P, grid, st);
+    if (c.NT == 64 && c.L == 8) return launch_tile_kernel<64, 8>(P, grid, st);
     return SPV_E_ARG;
 }
 
@@ -1066,6 +1391,7 @@ int dispatch_occupancy(const Cfg &c, int *per_sm)
     if (c.NT == 256 && c.L == 8) return occupancy<256, 8>(per_sm);
     if (c.NT == 128 && c.L == 16) return occupancy<128, 16>(per_sm);
     if (c.NT == 128 && c.L == 8) return occupancy<128, 8>(per_sm);
+    if (c.NT == 64 && c.L == 8) return occupancy<64, 8>(per_sm);
     return SPV_E_ARG;
 }
 
@@ -1141,6 +1467,7 @@ extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint3
     P.cap_rows = table->capacity_rows;
     P.status = status; P.err_row = err_row;
     P.out = out_words; P.validate = validate ? 1 : 0; P.recompute_bound = recompute_bound ? 1 : 0;
+    P.out_vec = out_words && ((((uintptr_t)out_words) - ((uintptr_t)batch->words)) & 15) == 0;
     P.max_spins = c.max_spins;
     P.stall_tile = c.stall_tile;
     P.stall_map_tile = c.stall_map_tile;
@@ -1178,7 +1505,7 @@ extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint3
 }
 
 // The tile shapes k_tile is built for, tried by the autotuner.
-static const int kTileShapes[][2] = {{4096, 256}, {8192, 512}, {2048, 256}, {2048, 128}, {1024, 128}};
+static const int kTileShapes[][2] = {{4096, 256}, {8192, 512}, {2048, 256}, {2048, 128}, {1024, 128}, {512, 64}};
 
 extern "C" int spv_autotune_batch(const spv_batch *batch, spv_table *table, uint32_t *status, int64_t *err_row,
                                   int validate, uint32_t *out_words, void *workspace, size_t workspace_bytes,

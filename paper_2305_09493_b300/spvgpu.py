@@ -288,7 +288,7 @@ def process(words, mod_off, *, validate=True, encode=False, recompute_bound=True
 
 
 # the tile shapes the library's autotuner tries
-TILE_SHAPES = ((4096, 256), (8192, 512), (2048, 256), (2048, 128), (1024, 128))
+TILE_SHAPES = ((4096, 256), (8192, 512), (2048, 256), (2048, 128), (1024, 128), (512, 64))
 
 
 def autotune_workspace_bytes(n_modules, n_words, arena_words=0):

@@ -96,7 +96,7 @@ def test_small_batch_ragged(gpu):
     check(gpu, w, off, dis=True)
 
 
-@pytest.mark.parametrize("tile,threads", [(4096, 256), (2048, 256), (2048, 128), (1024, 128)])
+@pytest.mark.parametrize("tile,threads", [(4096, 256), (8192, 512), (2048, 256), (2048, 128), (1024, 128), (512, 64)])
 def test_tile_configs(gpu, tile, threads):
     n_instr, n_k = synth.batch_shape(60, 3, median=3000, lo=200, hi=30000)
     w1, off1 = synth.batch(n_instr, n_k, 3)
@@ -104,6 +104,30 @@ def test_tile_configs(gpu, tile, threads):
     words = np.concatenate([w1, w2])
     offs = np.concatenate([off1, off1[-1] + off2[1:]])
     check(gpu, words, offs, cfg=gpu.make_config(tile_words=tile, threads=threads), dis=(tile == 2048 and threads == 128))
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_word_buffer_off_a_16_byte_boundary(gpu, shift):
+    """The word buffer starts 4, 8 or 12 bytes past a 16-byte boundary (a view
+    into a larger allocation), so every module's tiles are staged with a
+    different phase and the encoded words (in a buffer of another phase) are
+    stored word by word; exact against the oracle."""
+    n_instr, n_k = synth.batch_shape(30, 21, median=2000, lo=200, hi=20000)
+    w, off = synth.batch(n_instr, n_k, 21)
+    big = torch.zeros(len(w) + 8, dtype=torch.int32, device="cuda")
+    wt = big[shift:shift + len(w)]
+    wt.copy_(torch.from_numpy(w.view(np.int32)))
+    assert wt.data_ptr() % 16 == 4 * shift
+    o = torch.from_numpy(off).cuda()
+    for cfg in (None, gpu.make_config(tile_words=2048, threads=128), gpu.make_config(tile_words=512, threads=64)):
+        r = gpu.process(wt, o, validate=True, encode=True, cfg=cfg)
+        torch.cuda.synchronize()
+        d = oracle.decode(w, off)
+        assert_table_equal(r["table"].to_numpy(), d, len(off) - 1)
+        st, er = oracle.validate(w, off)
+        assert np.array_equal(r["status"].cpu().numpy().view(np.uint32), st)
+        assert np.array_equal(r["err_row"].cpu().numpy(), er)
+        assert np.array_equal(r["out"].cpu().numpy().view(np.uint32), oracle.encode(w, off, d, True))
 
 
 def test_per_module_path_matches(gpu):
