@@ -604,24 +604,27 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
                     }
                     hi_j -= 32;
                 }
-                // apply predecessors' maps from the anchor forward. When every
-                // tile between the anchor and this one was read in the last poll
-                // (one per lane), an inline map settles a marked entry without
-                // a map entry; otherwise the map entry is read (one read as 0 is
-                // not visible yet and is read again)
+                // apply predecessors' maps from the anchor forward, 32 tiles'
+                // states per read (the last poll's when it holds them all): a
+                // published exit is taken as it is, an inline map settles a
+                // marked entry, anything else reads the map entry (one read as
+                // 0 is not visible yet and is read again)
                 uint32_t xx = ax;
-                const bool in_regs = (hi_j == g - 1);
-                for (long long tt = anchor + 1; tt < g && !gave_up; tt++) {
+                for (long long t0 = anchor + 1; t0 < g && !gave_up; t0 += 32) {
+                  const bool in_regs = (hi_j == g - 1);
+                  const long long tl = t0 + lane;
+                  const unsigned long long stb = in_regs ? 0ull : (tl < g ? ld_relaxed(&P.tstate[tl]) : 0ull);
+                  for (long long tt = t0; tt < g && tt < t0 + 32 && !gave_up; tt++) {
                     {
                         uint32_t kt = (uint32_t)(tt - first);
                         uint32_t tb = kt * (uint32_t)T - ph;
                         if (xx == DEAD || xx >= tb + (uint32_t)T) continue;
-                        if (in_regs) {
-                            const unsigned long long stt = __shfl_sync(FULL, st_last, (int)(hi_j - tt));
-                            if ((stt & F_MASK) == F_FMAP && xx - tb < 32 && ((stt >> (xx - tb)) & 1ull)) {
-                                xx = tb + (uint32_t)((stt >> 32) & 0x3ffffu);
-                                continue;
-                            }
+                        const unsigned long long stt = in_regs ? __shfl_sync(FULL, st_last, (int)(hi_j - tt))
+                                                               : __shfl_sync(FULL, stb, (int)(tt - t0));
+                        if ((stt & F_MASK) == F_EXIT) { xx = (uint32_t)(stt & 0xffffffffu); continue; }
+                        if ((stt & F_MASK) == F_FMAP && xx - tb < 32 && ((stt >> (xx - tb)) & 1ull)) {
+                            xx = tb + (uint32_t)((stt >> 32) & 0x3ffffu);
+                            continue;
                         }
                         uint32_t val = xx - tb < 32 ? __shfl_sync(FULL, ld_relaxed32(&P.tmap[tt * NCAND + lane]), (int)((xx - tb) & 31u)) : 0u;
                         while (xx - tb < 32 && val == 0u) {
@@ -644,6 +647,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
                         if (gave_up) break;
                         xx = (uint32_t)(st & 0xffffffffu);
                     }
+                  }
                 }
                 entry = gave_up ? DEAD : (xx == DEAD ? DEAD : xx - tb_rel);
                 if (gave_up && lane == 0) s.timeout = 1;
