@@ -722,6 +722,14 @@ struct MainSmem {
     uint8_t ihdr[ITEMS];            // per item: a module's header item
     alignas(16) uint32_t wst[STAGE_WORDS];  // words [wa, wa + STAGE_WORDS) of the batch (wa: wlo aligned down)
     unsigned long long wlo, whi;
+    // per CTA, once: the opcode and enumerant names, each opcode's text form
+    // for the fast line writer, powers of ten, bit-enum tables
+    char names[spvt::NAME_POOL];
+    uint2 otx[256];
+    uint32_t pow10[10];
+    uint8_t bnp[spvt::NUM_BKINDS][16];   // literal parameters of the known bits of a mask's low 4 bits
+    uint8_t btl[spvt::NUM_BKINDS][16];   // text bytes of a mask of known bits ("None" for 0)
+    uint8_t bknown[spvt::NUM_BKINDS];    // the kind's known bits
     uint32_t cls_n[NSHAPE];
     uint32_t warp_tot[DNT / 32];
     long long tile;
@@ -729,6 +737,164 @@ struct MainSmem {
     int m0, nm;
     int gave_up;
 };
+
+// ---------------------------------------------------------------------------
+// the fast line form: an opcode in the fast operand form (fixed ids and
+// literals, then a tail of ids, literals, id pairs or one bit-enum word with
+// its literal parameters; no context-dependent literal), its word count
+// valid for the form, and no named id among its operands. Its length is
+// counted arithmetically and its text written backwards from the line's end,
+// digits straight from the values; every other line takes format_row. Both
+// give the same bytes (section 3.4.4's text form as format_row defines it).
+// ---------------------------------------------------------------------------
+constexpr uint32_t NOTFAST = 0xFFFFFFFFu;
+
+// otx[op]: x = name offset | name length << 16 | form << 24 (bit 0 fast text,
+// bits 1-3 tail, bit 4 the bit-enum word may be absent); y = id mask | fixed
+// words << 16 | result type / id flags (bits 1, 2) << 24 | bit-enum kind << 28
+__device__ void init_text_tables(MainSmem &s)
+{
+    const spvt::Tables &T = g_spv_tables;
+    for (int i = threadIdx.x; i < spvt::NAME_POOL; i += blockDim.x) s.names[i] = T.names[i];
+    for (int o = threadIdx.x; o < 256; o += blockDim.x) {
+        const spvt::OpDesc &d = T.ops[o];
+        bool ctx = false;
+        for (int q = 0; q < d.nprog; q++) if ((d.prog[q] & 0x7f) == spvt::A_CTX) ctx = true;
+        const uint32_t form = ((d.flags & 1) && (d.fast & 1) && !ctx) ? (uint32_t)d.fast : 0u;
+        s.otx[o] = make_uint2((uint32_t)d.name_off | ((uint32_t)d.name_len << 16) | (form << 24),
+                              (uint32_t)d.id_mask | ((uint32_t)d.nfixed << 16) | ((uint32_t)(d.flags & 6) << 24) |
+                                  ((uint32_t)d.bkind << 28));
+    }
+    if (threadIdx.x < 10) {
+        uint32_t v = 1;
+        for (uint32_t i = 0; i < threadIdx.x; i++) v *= 10u;
+        s.pow10[threadIdx.x] = v;
+    }
+    if (threadIdx.x < spvt::NUM_BKINDS * 16) {
+        const int kind = threadIdx.x >> 4, m = threadIdx.x & 15;
+        uint32_t known = 0, np = 0, tl = 0, nb = 0;
+        for (int b = 0; b < 32; b++) if (T.benum[kind][b].known) known |= 1u << b;
+        for (int b = 0; b < 4; b++)
+            if (((m >> b) & 1) && T.benum[kind][b].known) { np += T.benum[kind][b].nparam; tl += T.benum[kind][b].name_len; nb++; }
+        s.bnp[kind][m] = (uint8_t)np;
+        s.btl[kind][m] = (uint8_t)(m == 0 ? 4 : tl + nb - 1);
+        if (m == 0) s.bknown[kind] = (uint8_t)known;
+    }
+}
+
+// decimal digits of v: t = floor(bits(v) * 1233 / 4096) is the digit count
+// or one more than it
+__device__ __forceinline__ uint32_t dlen_s(const MainSmem &s, uint32_t v)
+{
+    const uint32_t u = v | 1u;                         // 0 prints like 1: one digit
+    const uint32_t t = ((32u - __clz(u)) * 1233u) >> 12;
+    return t + 1u - (u < s.pow10[t] ? 1u : 0u);
+}
+
+// an id that prints with its name (inline names on, a name recorded for it)
+__device__ __forceinline__ bool named_id(const RowCtx &c, uint32_t id)
+{
+    return c.named && id < c.bound && (c.slots || !((c.tab[3ull * c.bound + (id >> 5)] >> (id & 31)) & 1u));
+}
+
+// the line's length in the fast form, or NOTFAST
+__device__ uint32_t fast_len(const MainSmem &s, const RowCtx &c)
+{
+    const uint2 ot = s.otx[c.op < 256 ? c.op : 0];
+    const uint32_t form = ot.x >> 24;
+    if (c.op >= 256 || !(form & 1u)) return NOTFAST;
+    const uint32_t need = 1u + ((ot.y >> 16) & 0xffu), tail = (form >> 1) & 7u, wc = c.wc;
+    bool ok;
+    uint32_t mask = 0;
+    const uint32_t bk = ot.y >> 28;
+    if (tail == 4) {
+        if (wc == need) ok = (form & 16u) != 0;
+        else if (wc > need) { mask = c.iw[need]; ok = wc == need + 1u + s.bnp[bk][mask & 15u]; }
+        else ok = false;
+    } else {
+        ok = tail == 0 ? wc == need : (wc >= need && (tail != 3 || ((wc - need) & 1u) == 0));
+    }
+    if (!ok) return NOTFAST;
+    const uint32_t idm = ot.y & 0xffffu;
+    uint32_t len = ((ot.x >> 16) & 0xffu) + 1u + (((ot.y >> 24) & 4u) ? 2u : 0u);   // name, '\n', " = " past " "
+    for (uint32_t i = 1; i < need; i++) {
+        const uint32_t v = c.iw[i];
+        const uint32_t isid = (idm >> i) & 1u;
+        if (isid && named_id(c, v)) return NOTFAST;
+        len += 1u + isid + dlen_s(s, v);
+    }
+    if (tail == 1 || tail == 3) {
+        for (uint32_t i = need; i < wc; i++) {
+            const uint32_t v = c.iw[i];
+            if (named_id(c, v)) return NOTFAST;
+            len += 2u + dlen_s(s, v);
+        }
+    } else if (tail == 2) {
+        for (uint32_t i = need; i < wc; i++) len += 1u + dlen_s(s, c.iw[i]);
+    } else if (tail == 4 && wc > need) {
+        len += 1u + ((mask & ~(uint32_t)s.bknown[bk]) ? dlen_s(s, mask) : (uint32_t)s.btl[bk][mask & 15u]);
+        for (uint32_t i = need + 1; i < wc; i++) len += 1u + dlen_s(s, c.iw[i]);
+    }
+    return len;
+}
+
+__device__ __forceinline__ uint32_t put_dec_back(uint32_t e, uint32_t v)
+{
+    do { const uint32_t q = v / 10u; stext()[--e] = (char)('0' + (v - 10u * q)); v = q; } while (v);
+    return e;
+}
+__device__ __forceinline__ uint32_t put_name_back(const MainSmem &s, uint32_t e, uint32_t off, uint32_t len)
+{
+    for (uint32_t i = len; i > 0; i--) stext()[--e] = s.names[off + i - 1];
+    return e;
+}
+
+// the line of a fast-form row, written backwards so that it ends at byte end
+// of the shared text buffer
+__device__ void fast_write(const MainSmem &s, const RowCtx &c, uint32_t end)
+{
+    const uint2 ot = s.otx[c.op];
+    const uint32_t form = ot.x >> 24;
+    const uint32_t need = 1u + ((ot.y >> 16) & 0xffu), tail = (form >> 1) & 7u, wc = c.wc;
+    const uint32_t idm = ot.y & 0xffffu, fl = (ot.y >> 24) & 6u, bk = ot.y >> 28;
+    uint32_t e = end;
+    stext()[--e] = '\n';
+    if (tail == 1 || tail == 3) {
+        for (uint32_t i = wc; i > need; i--) { e = put_dec_back(e, c.iw[i - 1]); stext()[--e] = '%'; stext()[--e] = ' '; }
+    } else if (tail == 2) {
+        for (uint32_t i = wc; i > need; i--) { e = put_dec_back(e, c.iw[i - 1]); stext()[--e] = ' '; }
+    } else if (tail == 4 && wc > need) {
+        for (uint32_t i = wc; i > need + 1; i--) { e = put_dec_back(e, c.iw[i - 1]); stext()[--e] = ' '; }
+        const uint32_t mask = c.iw[need];
+        if (mask == 0) {
+            stext()[--e] = 'e'; stext()[--e] = 'n'; stext()[--e] = 'o'; stext()[--e] = 'N';
+        } else if (mask & ~(uint32_t)s.bknown[bk]) {
+            e = put_dec_back(e, mask);
+        } else {
+            for (int b = 31 - __clz(mask); b >= 0; b--) {
+                if (!((mask >> b) & 1u)) continue;
+                const spvt::EnDesc &en = g_spv_tables.benum[bk][b];
+                e = put_name_back(s, e, ((uint32_t)en.name_hi << 8) | en.name_lo, en.name_len);
+                if (mask & ((1u << b) - 1u)) stext()[--e] = '|';
+            }
+        }
+        stext()[--e] = ' ';
+    }
+    // fixed words after the result type and id, last first; then the result type
+    const uint32_t first = 1u + (fl & 2u ? 1u : 0u) + (fl & 4u ? 1u : 0u);
+    for (uint32_t i = need - 1; i >= first; i--) {
+        e = put_dec_back(e, c.iw[i]);
+        if ((idm >> i) & 1u) stext()[--e] = '%';
+        stext()[--e] = ' ';
+    }
+    if (fl & 2u) { e = put_dec_back(e, c.iw[1]); stext()[--e] = '%'; stext()[--e] = ' '; }
+    e = put_name_back(s, e, ot.x & 0xffffu, (ot.x >> 16) & 0xffu);
+    if (fl & 4u) {
+        stext()[--e] = ' '; stext()[--e] = '='; stext()[--e] = ' ';
+        e = put_dec_back(e, c.iw[(fl & 2u) ? 2 : 1]);
+        stext()[--e] = '%';
+    }
+}
 
 __device__ __forceinline__ bool make_ctx(const DP &P, const MainSmem &s, int j, int m, long long row, RowCtx &c,
                                          int walk_ok)
@@ -809,6 +975,7 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n_items = (long long)P.ctrl->n_items;
     const long long ntiles = (n_items + ITEMS - 1) / ITEMS;
+    init_text_tables(s);
     // a ticket is taken when its tile starts: a tile waits only on lower
     // tiles, whose holders are running, so the look-backs always end; a
     // ticket taken a tile ahead would hold back every later tile's look-back
@@ -958,7 +1125,14 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
                 if (s.ihdr[j]) len = P.dm[m].header_len;
                 else {
                     RowCtx c;
-                    if (make_ctx(P, s, j, m, i0 + j - m - 1, c, -1)) { CountSink k; format_row(k, c); len = k.n; ok = c.walk_ok; }
+                    if (make_ctx(P, s, j, m, i0 + j - m - 1, c, 1)) {
+                        const uint32_t fl = fast_len(s, c);
+                        if (fl != NOTFAST) { len = fl; ok = 2; }
+                        else {
+                            make_ctx(P, s, j, m, i0 + j - m - 1, c, -1);
+                            CountSink k; format_row(k, c); len = k.n; ok = c.walk_ok;
+                        }
+                    }
                 }
             }
             s.ilen[j] = len;
@@ -1001,8 +1175,14 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
                 for (int q = tid; q < ITEMS; q += DNT) {
                     int j = s.perm[q];
                     if (s.im[j] < 0 || s.ilen[j] == 0) continue;
-                    WriteSink k{s.ioff[j]};
-                    format_item(k, j);
+                    if (s.iok[j] == 2) {
+                        RowCtx c;
+                        make_ctx(P, s, j, s.im[j], i0 + j - s.im[j] - 1, c, 1);
+                        fast_write(s, c, s.ioff[j] + s.ilen[j]);
+                    } else {
+                        WriteSink k{s.ioff[j]};
+                        format_item(k, j);
+                    }
                 }
             }
             if (wid == 0) dis_lookback(P, s, t, total, lane, last_tile);
