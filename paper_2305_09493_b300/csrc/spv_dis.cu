@@ -71,7 +71,11 @@ struct DisMod {
     uint32_t status;         // S_OK / header status / S_CAPACITY
     uint32_t named;          // 1 when some OpName names an id of the module
     long long item_base;     // index of the module's header item
+    unsigned long long bloom;// bit name_hash(id) set for every named id (a superset test)
 };
+
+// one of 64 bits per id for the modules' named-id filters
+__device__ __forceinline__ uint32_t name_hash(uint32_t id) { return (id * 0x9E3779B1u) >> 26; }
 
 struct DP {
     const uint32_t *words;
@@ -560,6 +564,7 @@ __global__ void k_dis_premod(DP P)
         d.status = st;
         d.header_len = (st == S_OK && P.header) ? header_len(P.words + o) : 0;
         d.named = 0;
+        d.bloom = 0;
         long long fr = P.first_row[m];
         d.item_base = (fr < n_rows ? fr : n_rows) + m;
         P.dm[m] = d;
@@ -649,6 +654,7 @@ __global__ void k_dis_ids(DP P)
                 uint32_t target = __ldg(P.words + P.off[row] + 1);
                 if (target < bound) {
                     if (!namedq[q]) P.dm[m].named = 1;
+                    atomicOr(&P.dm[m].bloom, 1ull << name_hash(target));
                     atomicMin(&idtab_entry(tab, bound, slots, target, true)[0], local);
                     if (!slots) atomicAnd(&tab[3ull * bound + (target >> 5)], ~(1u << (target & 31)));
                 }
@@ -731,6 +737,8 @@ struct MainSmem {
     uint8_t btl[spvt::NUM_BKINDS][16];   // text bytes of a mask of known bits ("None" for 0)
     uint8_t bknown[spvt::NUM_BKINDS];    // the kind's known bits
     uint32_t cls_n[NSHAPE];
+    // the first MCACHE modules of the tile: what formatting reads of them
+    struct MC { uint32_t ok, bound, slots, named; unsigned long long bloom; long long arena_off, first; } mc[32];
     uint32_t warp_tot[DNT / 32];
     long long tile;
     unsigned long long base;
@@ -792,13 +800,14 @@ __device__ __forceinline__ uint32_t dlen_s(const MainSmem &s, uint32_t v)
 }
 
 // an id that prints with its name (inline names on, a name recorded for it)
-__device__ __forceinline__ bool named_id(const RowCtx &c, uint32_t id)
+__device__ __forceinline__ bool named_id(const RowCtx &c, uint32_t id, unsigned long long bloom)
 {
-    return c.named && id < c.bound && (c.slots || !((c.tab[3ull * c.bound + (id >> 5)] >> (id & 31)) & 1u));
+    return ((bloom >> name_hash(id)) & 1ull) && c.named && id < c.bound &&
+           (c.slots || !((c.tab[3ull * c.bound + (id >> 5)] >> (id & 31)) & 1u));
 }
 
 // the line's length in the fast form, or NOTFAST
-__device__ uint32_t fast_len(const MainSmem &s, const RowCtx &c)
+__device__ uint32_t fast_len(const MainSmem &s, const RowCtx &c, unsigned long long bloom)
 {
     const uint2 ot = s.otx[c.op < 256 ? c.op : 0];
     const uint32_t form = ot.x >> 24;
@@ -820,13 +829,13 @@ __device__ uint32_t fast_len(const MainSmem &s, const RowCtx &c)
     for (uint32_t i = 1; i < need; i++) {
         const uint32_t v = c.iw[i];
         const uint32_t isid = (idm >> i) & 1u;
-        if (isid && named_id(c, v)) return NOTFAST;
+        if (isid && named_id(c, v, bloom)) return NOTFAST;
         len += 1u + isid + dlen_s(s, v);
     }
     if (tail == 1 || tail == 3) {
         for (uint32_t i = need; i < wc; i++) {
             const uint32_t v = c.iw[i];
-            if (named_id(c, v)) return NOTFAST;
+            if (named_id(c, v, bloom)) return NOTFAST;
             len += 2u + dlen_s(s, v);
         }
     } else if (tail == 2) {
@@ -899,20 +908,31 @@ __device__ void fast_write(const MainSmem &s, const RowCtx &c, uint32_t end)
 __device__ __forceinline__ bool make_ctx(const DP &P, const MainSmem &s, int j, int m, long long row, RowCtx &c,
                                          int walk_ok)
 {
-    const DisMod &md = P.dm[m];
-    if (!md.ok) return false;
+    const int mi = m - s.m0;
+    if (mi < 32) {                       // the tile's first modules: from shared memory
+        const MainSmem::MC &mc = s.mc[mi];
+        if (!mc.ok) return false;
+        c.bound = mc.bound;
+        c.slots = mc.slots;
+        c.named = P.inline_names && mc.named;
+        c.tab = P.arena + mc.arena_off;
+        c.first = mc.first;
+    } else {
+        const DisMod &md = P.dm[m];
+        if (!md.ok) return false;
+        c.bound = md.bound;
+        c.slots = md.slots;
+        c.named = P.inline_names && md.named;
+        c.tab = P.arena + md.arena_off;
+        c.first = P.first_row[m];
+    }
     c.iw = s.irel[j] != NOSTAGE ? s.wst + s.irel[j] : P.words + P.off[row];
     c.wc = s.iwc[j];
     c.op = s.iop[j];
-    c.bound = md.bound;
-    c.slots = md.slots;
-    c.named = P.inline_names && md.named;
-    c.tab = P.arena + md.arena_off;
     c.words = P.words;
     c.off = P.off;
     c.opcol = P.op;
     c.inline_names = P.inline_names != 0;
-    c.first = P.first_row[m];
     if (walk_ok >= 0) c.walk_ok = walk_ok != 0;
     else {
         c.walk_ok = true;
@@ -1001,6 +1021,12 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
                                          : (m0 + nm < P.n_mod ? P.dm[m0 + nm].item_base : n_items);
                     b -= i0;
                     s.ibase[j] = (int)(b < -1 ? -1 : (b > ITEMS + 1 ? ITEMS + 1 : b));
+                }
+                if (lane < nm) {
+                    const DisMod &md = P.dm[m0 + lane];
+                    MainSmem::MC &mc = s.mc[lane];
+                    mc.ok = md.ok; mc.bound = md.bound; mc.slots = md.slots; mc.named = md.named;
+                    mc.bloom = md.bloom; mc.arena_off = md.arena_off; mc.first = P.first_row[m0 + lane];
                 }
             }
         }
@@ -1126,7 +1152,9 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
                 else {
                     RowCtx c;
                     if (make_ctx(P, s, j, m, i0 + j - m - 1, c, 1)) {
-                        const uint32_t fl = fast_len(s, c);
+                        const int mi = m - s.m0;
+                        const unsigned long long bloom = mi < 32 ? s.mc[mi].bloom : P.dm[m].bloom;
+                        const uint32_t fl = fast_len(s, c, bloom);
                         if (fl != NOTFAST) { len = fl; ok = 2; }
                         else {
                             make_ctx(P, s, j, m, i0 + j - m - 1, c, -1);
