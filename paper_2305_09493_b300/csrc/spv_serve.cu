@@ -2,10 +2,11 @@
 //
 // Modules arrive one by one (a JIT backend emitting kernels, the paper's use
 // case in section 4). A scheduler thread forms a batch from every waiting
-// module whenever one of two batch slots is free, and runs decode + validate
-// + disassembly on it (spv_process_batch, spv_disassemble_batch) on that
-// slot's stream; stream callbacks wake the scheduler when a batch's kernels
-// and copies finish. Requests that arrive while a batch is on the GPU wait
+// module whenever one of NSLOT batch slots is free, and runs decode +
+// validate + disassembly on it (spv_process_batch, spv_disassemble_batch) on
+// that slot's stream; a small kernel then writes the batch's text straight
+// into mapped pinned host memory, and one stream callback per batch wakes
+// the scheduler when its kernels and copies finish. Requests that arrive while a batch is on the GPU wait
 // for the next free slot. Admission is by device footprint: a module of n
 // words holds 28 * n + 64 bytes of the device pool (words and decoded
 // table) from submit to release.
@@ -37,6 +38,31 @@ uint64_t now_ns()
 }
 
 size_t up(size_t x) { return (x + 255) & ~size_t(255); }
+
+constexpr int NSLOT = 3;                 // batches on the GPU at once
+
+// the batch's text (text_off[n] bytes, when it fits cap) to pinned host
+// memory mapped into the device's address space: 16-byte stores where the
+// two buffers share a phase, bytes elsewhere
+__global__ void k_text_to_host(const char *src, const uint64_t *total_at, char *dst, uint64_t cap)
+{
+    const uint64_t total = *total_at;
+    if (total > cap) return;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (((((uintptr_t)src) ^ ((uintptr_t)dst)) & 15) == 0) {
+        const uint64_t head = (16 - (((uintptr_t)src) & 15)) & 15;
+        const uint64_t h = head < total ? head : total;
+        for (uint64_t i = t0; i < h; i += stride) dst[i] = src[i];
+        const uint64_t nv = (total - h) / 16;
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src + h);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst + h);
+        for (uint64_t i = t0; i < nv; i += stride) d4[i] = s4[i];
+        for (uint64_t i = h + 16 * nv + t0; i < total; i += stride) dst[i] = src[i];
+    } else {
+        for (uint64_t i = t0; i < total; i += stride) dst[i] = src[i];
+    }
+}
 
 // first-fit allocator over the byte range [0, size)
 class Arena {
@@ -93,7 +119,7 @@ struct Batch {
     int error = SPV_SUCCESS;
     std::atomic<int> signaled{0};
     int handled = 0;
-    int phase = 0;                       // 1 kernels + small copies, 2 text copy
+    int phase = 0;                       // 1 kernels, text and small copies; 2 text copied again (past its first room)
     int live = 0;
     Region dev, tmp, text_extra, pin_small, pin_text;
     // device pointers
@@ -121,8 +147,9 @@ struct spv_server {
     char *hpool = nullptr;
     size_t hpool_bytes = 0;
     Arena harena;
-    cudaStream_t st[2] = {nullptr, nullptr};
-    bool slot_busy[2] = {false, false};
+    char *hpool_dev = nullptr;           // the pinned pool's address on the device
+    cudaStream_t st[NSLOT] = {};
+    bool slot_busy[NSLOT] = {};
     std::mutex mu;
     std::condition_variable cv, done_cv;
     std::deque<Req *> queue;
@@ -213,8 +240,9 @@ bool launch(spv_server *s, int slot, std::unique_lock<std::mutex> &lk)
     bool ok = dalloc(s, b->dev, persistent_bytes(n, words));
     ok = ok && dalloc(s, b->tmp, tmp_bytes);
     ok = ok && halloc(s, b->pin_small, small);
+    ok = ok && halloc(s, b->pin_text, b->text_cap + 1);
     if (!ok) {
-        dfree(s, b->dev); dfree(s, b->tmp); hfree(s, b->pin_small);
+        dfree(s, b->dev); dfree(s, b->tmp); hfree(s, b->pin_small); hfree(s, b->pin_text);
         for (auto it = take.rbegin(); it != take.rend(); ++it) s->queue.push_front(*it);
         delete b;
         return false;
@@ -234,6 +262,7 @@ bool launch(spv_server *s, int slot, std::unique_lock<std::mutex> &lk)
     Carver hv{s->hpool + b->pin_small.off};
     b->h_modoff = hv.take<int64_t>(n + 1); b->h_toff = hv.take<uint64_t>(n + 1); b->h_first = hv.take<int64_t>(n + 1);
     b->h_status = hv.take<uint32_t>(n); b->h_ninstr = hv.take<uint32_t>(n); b->h_err = hv.take<int64_t>(n);
+    b->h_text = s->hpool + b->pin_text.off;
     cudaStream_t st = s->st[slot];
     // module offsets, and the words: one copy per run of contiguous staging
     int64_t o = 0;
@@ -267,6 +296,11 @@ bool launch(spv_server *s, int slot, std::unique_lock<std::mutex> &lk)
     if (e == SPV_SUCCESS)
         e = spv_disassemble_batch(&bt, &tb, &opts, b->d_text, b->text_cap, b->d_toff, b->d_dst, b->d_dws,
                                   b->dws_bytes, 0, (spv_stream_t)st);
+    if (e == SPV_SUCCESS) {
+        const int blocks = (int)std::min<uint64_t>(1024, (b->text_cap / 16 + 255) / 256 + 1);
+        k_text_to_host<<<blocks, 256, 0, st>>>(b->d_text, b->d_toff + n, s->hpool_dev + b->pin_text.off, b->text_cap);
+        if (cudaPeekAtLastError() != cudaSuccess) e = SPV_E_CUDA;
+    }
     if (e == SPV_SUCCESS) {
         cudaMemcpyAsync(b->h_status, b->d_status, 4 * (size_t)n, cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(b->h_err, b->d_err, 8 * (size_t)n, cudaMemcpyDeviceToHost, st);
@@ -322,12 +356,17 @@ void advance(spv_server *s, Batch *b)
             if (cudaLaunchHostFunc(st, on_stage, b) != cudaSuccess) { b->error = SPV_E_CUDA; complete(s, b); }
             return;                     // phase 1 again, now with room for the text
         }
-        if (!halloc(s, b->pin_text, total + 1)) { b->error = SPV_E_BUSY; complete(s, b); return; }
-        b->h_text = s->hpool + b->pin_text.off;
-        if (total) cudaMemcpyAsync(b->h_text, b->d_text, total, cudaMemcpyDeviceToHost, st);
-        b->phase = 2;
-        if (cudaLaunchHostFunc(st, on_stage, b) != cudaSuccess) { b->error = SPV_E_CUDA; complete(s, b); }
-        return;
+        if (total + 1 > b->pin_text.bytes) {
+            // the text outgrew its first room: copy it into a pinned region of its size
+            hfree(s, b->pin_text);
+            if (!halloc(s, b->pin_text, total + 1)) { b->error = SPV_E_BUSY; complete(s, b); return; }
+            b->h_text = s->hpool + b->pin_text.off;
+            if (total) cudaMemcpyAsync(b->h_text, b->d_text, total, cudaMemcpyDeviceToHost, st);
+            b->phase = 2;
+            if (cudaLaunchHostFunc(st, on_stage, b) != cudaSuccess) { b->error = SPV_E_CUDA; complete(s, b); }
+            return;
+        }
+        // the text is in pinned memory already (written by k_text_to_host)
     }
     complete(s, b);
 }
@@ -351,7 +390,7 @@ void scheduler(spv_server *s)
         }
         if (s->stop && s->queue.empty() && s->inflight.empty()) break;
         bool launched = false;
-        for (int slot = 0; slot < 2 && !s->queue.empty(); slot++)
+        for (int slot = 0; slot < NSLOT && !s->queue.empty(); slot++)
             if (!s->slot_busy[slot]) launched |= launch(s, slot, lk);
         if (!launched) s->cv.wait_for(lk, std::chrono::microseconds(50));
     }
@@ -397,15 +436,18 @@ extern "C" spv_server *spv_serve_create(const spv_serve_cfg *cfg)
     size_t per_batch = spv_workspace_bytes(s->cfg.max_batch_modules, W, 0, &small_tiles) +
                        spv_dis_workspace_bytes(s->cfg.max_batch_modules, W, W, 0) + 12ull * W + 64ull * 4096 +
                        64ull * s->cfg.max_batch_modules + (1 << 20);
-    s->dpool_bytes = s->cfg.hbm_cap_bytes + 2 * per_batch + 28ull * W;
+    s->dpool_bytes = s->cfg.hbm_cap_bytes + NSLOT * per_batch + 28ull * W;
     s->hpool_bytes = s->cfg.hbm_cap_bytes / 2 + (64ull << 20);
     if (cudaMalloc((void **)&s->dpool, s->dpool_bytes) != cudaSuccess) { delete s; return nullptr; }
-    if (cudaHostAlloc((void **)&s->hpool, s->hpool_bytes, cudaHostAllocDefault) != cudaSuccess) {
+    if (cudaHostAlloc((void **)&s->hpool, s->hpool_bytes, cudaHostAllocMapped) != cudaSuccess) {
         cudaFree(s->dpool); delete s; return nullptr;
+    }
+    if (cudaHostGetDevicePointer((void **)&s->hpool_dev, s->hpool, 0) != cudaSuccess) {
+        cudaFree(s->dpool); cudaFreeHost(s->hpool); delete s; return nullptr;
     }
     s->darena.init(s->dpool_bytes);
     s->harena.init(s->hpool_bytes);
-    for (int k = 0; k < 2; k++) cudaStreamCreateWithFlags(&s->st[k], cudaStreamNonBlocking);
+    for (int k = 0; k < NSLOT; k++) cudaStreamCreateWithFlags(&s->st[k], cudaStreamNonBlocking);
     s->th = std::thread(scheduler, s);
     return s;
 }
@@ -414,17 +456,24 @@ extern "C" int spv_serve_submit(spv_server *s, const uint32_t *host_words, int64
 {
     if (!s || !ticket || n_words < 0 || (n_words && !host_words)) return SPV_E_ARG;
     uint64_t fp = 28ull * (uint64_t)n_words + 64;
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (s->stop) return SPV_E_ARG;
-    if (s->committed + fp > s->cfg.hbm_cap_bytes) return SPV_E_BUSY;
-    Req *r = new Req();
-    r->n_words = n_words;
-    if (!halloc(s, r->stage, 4 * (size_t)n_words)) { delete r; return SPV_E_BUSY; }
+    const uint64_t t_submit = now_ns();
+    Req *r = nullptr;
+    {
+        // admission and the staging region under the lock; the copy into it
+        // outside, so that the scheduler is not held up by it
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return SPV_E_ARG;
+        if (s->committed + fp > s->cfg.hbm_cap_bytes) return SPV_E_BUSY;
+        r = new Req();
+        r->n_words = n_words;
+        if (!halloc(s, r->stage, 4 * (size_t)n_words)) { delete r; return SPV_E_BUSY; }
+        r->footprint = fp;
+        s->committed += fp;
+    }
     if (n_words) memcpy(s->hpool + r->stage.off, host_words, 4 * (size_t)n_words);
+    std::lock_guard<std::mutex> lk(s->mu);
     r->ticket = s->next_ticket++;
-    r->footprint = fp;
-    r->submit_ns = now_ns();
-    s->committed += fp;
+    r->submit_ns = t_submit;
     s->reqs[r->ticket] = r;
     s->queue.push_back(r);
     *ticket = r->ticket;
@@ -485,7 +534,7 @@ extern "C" void spv_serve_destroy(spv_server *s)
     }
     s->cv.notify_all();
     if (s->th.joinable()) s->th.join();
-    for (int k = 0; k < 2; k++) if (s->st[k]) { cudaStreamSynchronize(s->st[k]); cudaStreamDestroy(s->st[k]); }
+    for (int k = 0; k < NSLOT; k++) if (s->st[k]) { cudaStreamSynchronize(s->st[k]); cudaStreamDestroy(s->st[k]); }
     std::vector<Batch *> batches;
     for (auto &kv : s->reqs) {
         Batch *b = kv.second->batch;
