@@ -44,6 +44,7 @@ def parse(argv=None):
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-per-module", action="store_true", help="skip the per-module comparison leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bins", action="store_true", help="skip the size-bin leg (tile sweep, autotuner, CUDA graph)")
     ap.add_argument("--modules", type=int, default=10_000, help="modules in the batch workload")
     ap.add_argument("--serve-rates", default="5000,10000,20000,50000",
                     help="Poisson arrival rates of the serve legs (modules/s, comma-separated)")
@@ -327,21 +328,16 @@ def run_reference(args):
 BIN_INSTR = (200, 2_000, 20_000, 50_000)
 
 
-def run_bins(args):
+def bins_leg(args, spvgpu, synth, dev):
     """Size bins (1,000 modules each at 200 / 2k / 20k / 50k instructions, 1-8
     kernels): per bin every tile shape of spv_process_batch timed, the
     autotuner's pick, and the whole step (decode + validate + encode with the
     picked shape, then disassemble) captured once in a CUDA graph and
     replayed; against the same decode + validate + encode with one launch
-    sequence per module."""
+    sequence per module. Returns (bins, words, step ms, launches)."""
     import torch
-    from paper_2305_09493_b300 import build, spvgpu, synth
-    build.build()
-    spvgpu.load()
-    dev = torch.device("cuda", torch.cuda.current_device())
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
     bins, tot_words, tot_ms = [], 0, 0.0
-    clocks = Clocks(torch.cuda.current_device())
     launches = 0
     for b, ni in enumerate(BIN_INSTR):
         rng = np.random.default_rng(100 + b)
@@ -369,6 +365,7 @@ def run_bins(args):
                 torch.cuda.synchronize()
                 t += e0.elapsed_time(e1)
             sweep[f"{tw}x{nt}"] = t / 3
+            del ws
         best, best_ms, _ = spvgpu.autotune(words, mod_off, table=table, out=out, reps=3)
         ws = spvgpu.Workspace(M, W, dev, 0, best)
         dws = spvgpu.DisWorkspace(M, W, W, dev)
@@ -411,13 +408,25 @@ def run_bins(args):
         bins.append({"instr_per_module": ni, "modules": M, "words": W, "text_bytes": L,
                      "sweep_process_ms": {k: round(v, 4) for k, v in sweep.items()},
                      "autotuned": f"{best.tile_words}x{best.threads}", "autotuned_process_ms": best_ms,
-                     "step_ms": step_ms, "gbs": 4 * W / (step_ms * 1e-3) / 1e9,
+                     "graph_step_ms": step_ms, "graph_step_gbs": 4 * W / (step_ms * 1e-3) / 1e9,
                      "process_gbs": 4 * W / (best_ms * 1e-3) / 1e9,
                      "per_module_process_gbs": 4 * W / (pm_ms * 1e-3) / 1e9, "all_status_ok": ok})
         tot_words += W
         tot_ms += step_ms
         del words, mod_off, table, out, ws, wsp, dws, text, g, r, dst
         torch.cuda.empty_cache()
+    return bins, tot_words, tot_ms, launches
+
+
+def run_bins(args):
+    """The size-bin workload alone (bins_leg), as its own JSON line."""
+    import torch
+    from paper_2305_09493_b300 import build, spvgpu, synth
+    build.build()
+    spvgpu.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    clocks = Clocks(torch.cuda.current_device())
+    bins, tot_words, tot_ms, launches = bins_leg(args, spvgpu, synth, dev)
     clk = clocks.stop()
     line = {"metric": METRIC, "value": 4 * tot_words / (tot_ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True,
@@ -723,6 +732,15 @@ def main():
         serve = {"scope": "decode+validate+disassemble per module, Poisson arrivals, latency from arrival to completion",
                  "cap_gb": args.serve_cap_gb, "seconds_per_rate": args.serve_seconds,
                  "per_launch_seconds_per_rate": args.serve_per_launch_seconds, "legs": legs}
+    bins = None
+    if not args.no_bins and world == 1 and args.workload == "batch":
+        from paper_2305_09493_b300 import synth as _synth
+        del table, ws, out, dws, text_buf, e_words, e_off, words, mod_off, aws, a_words
+        torch.cuda.empty_cache()
+        b_list, b_words, b_ms, b_launch = bins_leg(args, spvgpu, _synth, dev)
+        bins = {"scope": "4 size bins x 1,000 modules; per bin the tile-shape sweep, the autotuner's pick, the "
+                         "whole step in one CUDA graph, and one launch sequence per module",
+                "graph_steps_gbs": 4 * b_words / (b_ms * 1e-3) / 1e9, "bins": b_list}
     if rank != 0:
         if world > 1:
             torch.distributed.barrier()
@@ -751,6 +769,7 @@ def main():
         "assemble": asm_leg,
         "build": bld_leg,
         "serve": serve,
+        "size_bins": bins,
         "clocks": clk,
         "gpu_launches": launches,
     }
