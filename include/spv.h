@@ -118,7 +118,14 @@ typedef struct spv_config {
                                    states, so the waits of the tiles after it run out; with n < 0, tile
                                    -n-1 announces its tile map but never writes the map's entries, its
                                    exit or its row count, so a later tile of its module waits on a map
-                                   entry that nothing writes */
+                                   entry that nothing writes (either hook turns speculation off) */
+    int32_t no_speculation;     /* 1: every tile after a module's first finds its entry by the look-back
+                                   over its predecessors. 0 (default): a tile whose guessed instruction
+                                   starts form a chain takes its first guessed start as its entry and
+                                   publishes its exit and row count at once, checking the guess against
+                                   its predecessor's exit at the end; if any check fails the call redoes
+                                   the batch without speculation (on the same stream, same outputs) */
+    int32_t reserved;           /* 0 */
 } spv_config;
 
 /* Workspace bytes needed by spv_process_batch / spv_decode_batch /

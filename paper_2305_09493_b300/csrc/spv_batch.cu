@@ -83,7 +83,13 @@ struct Params {
     int table_mode;                // validating a caller's table: never write its columns
     int tile_words;                // words per tile of k_tile
     int out_vec;                   // out and words share their 16-byte phase: 16-byte stores
+    int spec;                      // tiles may take their first guessed start as their entry
+    int rerun;                     // the second round: every kernel returns unless a guess failed
 };
+
+// a kernel of the second round has nothing to do unless the first round's
+// entry guesses failed somewhere
+__device__ __forceinline__ bool skip_round(const Params &P) { return P.rerun && !P.ctrl->spec_failed; }
 
 // words from the 16-byte boundary below word o of the batch to that word
 __host__ __device__ inline uint32_t word_phase(const uint32_t *words, long long o)
@@ -98,6 +104,7 @@ __host__ __device__ inline uint32_t word_phase(const uint32_t *words, long long 
 // ---------------------------------------------------------------------------
 __global__ void k_prepass_mod(Params P, int tile_words)
 {
+    if (skip_round(P)) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long mm = blockIdx.x * (long long)blockDim.x + threadIdx.x; mm < P.n_modules; mm += stride) {
         const int m = (int)mm;
@@ -129,6 +136,7 @@ __global__ void k_prepass_mod(Params P, int tile_words)
 
 __global__ void __launch_bounds__(1024) k_prepass_scan(Params P)
 {
+    if (skip_round(P)) return;
     __shared__ unsigned long long s_tiles[32], s_arena[32];
     __shared__ unsigned long long s_base_tiles, s_base_arena;
     int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -179,6 +187,7 @@ __global__ void __launch_bounds__(1024) k_prepass_scan(Params P)
         P.ctrl->timeout = 0;
         P.ctrl->total_rows = 0;
         P.ctrl->n_fix = 0;
+        if (!P.rerun) P.ctrl->spec_failed = 0;
     }
 }
 
@@ -186,6 +195,7 @@ __global__ void __launch_bounds__(1024) k_prepass_scan(Params P)
 // look-back states and map entries (0: not written); clears the id arena
 __global__ void k_tile_setup(Params P)
 {
+    if (skip_round(P)) return;
     unsigned long long nt = P.ctrl->n_tiles;
     long long stride = (long long)gridDim.x * blockDim.x;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < (long long)nt; g += stride) {
@@ -267,7 +277,7 @@ struct TileSmem {
     long long mod_base;
     int m;
     uint32_t k, end_s, tile_n, hdr, ph;
-    uint32_t entry, exitp, exitX, cnt1, cnt2;
+    uint32_t entry, exitp, exitX, cnt1, cnt2, xfirst;
     int need_exact;
     int count_pub;                  // the row count is published already
     unsigned long long row_base;
@@ -296,6 +306,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int lo = tid * L;
     const spvt::Tables &TB = g_spv_tables;
+    if (skip_round(P)) return;
 
     // per-opcode tables, once per CTA
     for (int o = tid; o < 257; o += NT) {
@@ -351,7 +362,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
                 s.n_cap = s.n_mm = s.n_ep = s.n_fn = 0;
                 s.decl_lo = s.decl_hi = s.req_lo = s.req_hi = 0;
                 s.max_rid = 0; s.flags = 0; s.n_ids = 0; s.vnext = 0;
-                s.cnt1 = 0; s.cnt2 = 0; s.exitX = DEAD; s.need_exact = 0; s.count_pub = 0;
+                s.cnt1 = 0; s.cnt2 = 0; s.exitX = DEAD; s.need_exact = 0; s.count_pub = 0; s.xfirst = DEAD;
             }
         }
         for (int i = tid; i < T / 32; i += NT) s.far[i] = 0u;
@@ -464,14 +475,33 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
             r1 = __reduce_add_sync(FULL, r1);
             r2 = __reduce_add_sync(FULL, r2);
             if (lane == 0) { atomicAdd(&s.cnt1, r1); atomicAdd(&s.cnt2, r2); }
+            if (X) atomicMin(&s.xfirst, (uint32_t)(lo + __ffs(X) - 1));
         }
         __syncthreads();
         const uint32_t exitX = s.exitX;
-        bool fast = false;
+        bool fast = false, spec_tile = false;
         {
             const uint32_t c1 = s.cnt1, c2 = s.cnt2;
             const uint32_t nA = c1 & 0xffffu, nB = c1 >> 16, nE = c2 & 0xffffu, nX = c2 >> 16;
             fast = live && (nX == 0 || (nA == 1 && nB == 0 && nE == 1 && exitX <= end_s));
+            // a later tile of its module whose guessed starts form a chain takes
+            // the chain's first start as its entry: its exit and row count are
+            // known now; the guess is checked against the predecessor's exit at
+            // the end of the tile
+            spec_tile = P.spec && fast && k > 0 && nX > 0;
+            // a guessed chain that holds the tile's entry (its first start when
+            // guessing, word 5 of a module's first tile) gives the tile's exit
+            // and row count at once: published here, before anything else of
+            // the tile, since every later tile waits on the count
+            if (tid == 0 && fast && nX > 0 && g != P.stall_tile && g != P.stall_map_tile) {
+                const uint32_t e0 = ph + 5;
+                const bool first_on_chain = k == 0 && e0 < tile_n && ((s.X[e0 / L] >> (e0 % L)) & 1u);
+                if (spec_tile || first_on_chain) {
+                    st_relaxed(&P.tstate[g], F_EXIT | (unsigned long long)(exitX + tb_rel));
+                    st_relaxed(&P.cstate[g], (g == 0 ? F_EXIT : F_MAP) | (unsigned long long)nX);
+                    s.count_pub = 2;          // exit and count published
+                }
+            }
         }
 
         // exact path: per-position exits of each segment (backward pass),
@@ -524,8 +554,10 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
         //    for the tile's entry; the tile's exit, published. Meanwhile the
         //    other warps encode.
         if (wid == 0) {
-            uint32_t x;
-            if (fast) {
+            uint32_t x = UNRES;
+            if (spec_tile) {
+                // no map: later tiles read this tile's exit
+            } else if (fast) {
                 // a candidate entry on the guessed chain leaves with it; any
                 // other is followed a few steps until it joins the chain,
                 // dies or leaves the tile (else the map cannot tell)
@@ -552,7 +584,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
             const long long first = g - (long long)k;
             const bool stalled = (g == P.stall_tile);
             const bool map_only = (g == P.stall_map_tile);
-            const bool need_lookback = live && k > 0;
+            const bool need_lookback = live && k > 0 && !spec_tile;
             if (need_lookback && !stalled) {
                 // a map entry of a tile after a module's first is never 0 (an
                 // exit lies past the tile's start, DEAD and UNRES are not 0),
@@ -570,6 +602,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
             uint32_t entry;
             if (!live) entry = DEAD;
             else if (k == 0) entry = ph + 5;
+            else if (spec_tile) entry = s.xfirst;
             else {
                 // find the nearest predecessor with a published exit
                 long long hi_j = g - 1;
@@ -665,7 +698,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
                 }
                 s.entry = entry;
                 s.exitp = xw;
-                if (known_exit && live && g != P.stall_tile && g != P.stall_map_tile) {
+                if (known_exit && live && g != P.stall_tile && g != P.stall_map_tile && s.count_pub != 2) {
                     const uint32_t mx = xw == DEAD ? DEAD : xw + tb_rel;
                     st_relaxed(&P.tstate[g], F_EXIT | (unsigned long long)mx);
                 }
@@ -674,7 +707,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
             // the tile's row count, published as soon as its entry is known: the
             // guessed chain's starts from the entry on (none without a live
             // entry). Every later tile's first row waits on this count.
-            if (!live || entry == DEAD || (fast && s.need_exact == 0)) {
+            if (s.count_pub == 0 && (!live || entry == DEAD || (fast && s.need_exact == 0))) {
                 uint32_t c = 0;
                 if (live && entry != DEAD && entry < tile_n) {
                     for (int t = lane; t < NT; t += 32) {
@@ -964,6 +997,21 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
             if (lane == 0 && rmax) atomicMax(&s.max_rid, rmax);
         }
         __syncthreads();
+        // the entry guess of a speculating tile against its predecessor's exit
+        if (spec_tile && tid == 0) {
+            unsigned long long st = 0;
+            long long spins = 0;
+            for (;;) {
+                st = ld_relaxed(&P.tstate[g - 1]);
+                if ((st & F_MASK) == F_EXIT) break;
+                if (++spins > P.max_spins) { s.timeout = 1; break; }
+                spin_pause();
+            }
+            if ((st & F_MASK) == F_EXIT) {
+                const uint32_t xp = (uint32_t)(st & 0xffffffffu);
+                if (xp == DEAD || xp - tb_rel != s.xfirst) atomicExch(&P.ctrl->spec_failed, 1u);
+            }
+        }
         // 6. flush the tile's aggregates to the module
         if (tid == 0) {
             ModState *ms = &P.ms[m];
@@ -993,6 +1041,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
 // ---------------------------------------------------------------------------
 __global__ void k_id_popcount(Params P)
 {
+    if (skip_round(P)) return;
     const long long aw = (long long)P.ctrl->arena_used;
     const int CH = 64;
     const long long nch = (aw + CH - 1) / CH;
@@ -1045,6 +1094,7 @@ __device__ void module_status(const Params &P, int m, unsigned long long key, ui
 
 __global__ void k_finalize(Params P)
 {
+    if (skip_round(P)) return;
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= P.n_modules) return;
     if (!P.table_mode) {
@@ -1090,6 +1140,7 @@ constexpr int FIX_HASH = 4096;
 
 __global__ void __launch_bounds__(FIX_NT) k_fixup(Params P)
 {
+    if (skip_round(P)) return;
     __shared__ unsigned long long s_best;
     __shared__ uint32_t h_key[FIX_HASH];
     __shared__ uint32_t h_min[FIX_HASH];
@@ -1316,7 +1367,7 @@ Layout make_layout(int n_mod, long long n_words, long long arena_words, int tile
     return L;
 }
 
-struct Cfg { int T, NT, L, ctas_per_sm, per_module; long long max_spins, stall_tile, stall_map_tile; };
+struct Cfg { int T, NT, L, ctas_per_sm, per_module; long long max_spins, stall_tile, stall_map_tile; int spec; };
 
 // A tile shape left unset (tile_words and threads both 0) follows the batch:
 // batches of small modules (mean under 4,096 words) take 2,048-word tiles
@@ -1324,7 +1375,7 @@ struct Cfg { int T, NT, L, ctas_per_sm, per_module; long long max_spins, stall_t
 // 1,000-module bins of 200 to 50,000 instructions).
 int resolve_cfg(const spv_config *c, Cfg *out, int n_modules, long long n_words)
 {
-    Cfg r{4096, 256, 16, 0, 0, 1LL << 20, -1, -1};
+    Cfg r{4096, 256, 16, 0, 0, 1LL << 20, -1, -1, 1};
     const bool auto_shape = !c || (!c->tile_words && !c->threads);
     if (auto_shape && n_modules > 0 && n_words / n_modules < 4096) { r.T = 2048; r.NT = 128; }
     if (c) {
@@ -1336,6 +1387,7 @@ int resolve_cfg(const spv_config *c, Cfg *out, int n_modules, long long n_words)
         if (c->max_spins) r.max_spins = c->max_spins;
         if (c->test_stall_tile > 0) r.stall_tile = c->test_stall_tile - 1;
         if (c->test_stall_tile < 0) r.stall_map_tile = -c->test_stall_tile - 1;
+        if (c->no_speculation || c->test_stall_tile) r.spec = 0;
     }
     if (r.NT != 64 && r.NT != 128 && r.NT != 256 && r.NT != 512) return SPV_E_ARG;
     if (r.T % r.NT) return SPV_E_ARG;
@@ -1475,37 +1527,51 @@ extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint3
     P.max_spins = c.max_spins;
     P.stall_tile = c.stall_tile;
     P.stall_map_tile = c.stall_map_tile;
-    SPV_LAUNCH("k_prepass_mod", st, k_prepass_mod<<<sm_count() * 4, 256, 0, st>>>(P, c.T));
-    SPV_LAUNCH("k_prepass_scan", st, k_prepass_scan<<<1, 1024, 0, st>>>(P));
     int nsm = sm_count();
-    SPV_LAUNCH("k_tile_setup", st, k_tile_setup<<<nsm * 4, 256, 0, st>>>(P));
-    if (cudaPeekAtLastError() != cudaSuccess) return SPV_E_CUDA;
-    int rc;
-    if (!c.per_module) {
-        int per_sm = c.ctas_per_sm;
-        if (per_sm <= 0) { if (dispatch_occupancy(c, &per_sm)) return SPV_E_CUDA; if (per_sm < 1) per_sm = 1; }
-        P.persistent = 1;
-        rc = dispatch_tile(P, c, nsm * per_sm, st);
-    } else {
+    std::vector<int64_t> off;
+    if (c.per_module) {
         // comparison path: one launch per module, each CTA one tile
-        std::vector<int64_t> off(batch->n_modules + 1);
+        off.resize(batch->n_modules + 1);
         if (cudaMemcpyAsync(off.data(), batch->mod_off, 8 * off.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return SPV_E_CUDA;
-        P.persistent = 0;
-        rc = 0;
-        for (int m = 0; m < batch->n_modules && !rc; m++) {
-            long long len = off[m + 1] - off[m];
-            long long nt = len > 0 ? (len + c.T - 1) / c.T : 1;
-            rc = dispatch_tile(P, c, (int)nt, st);
-        }
     }
-    if (rc) return rc;
-    int nb = (batch->n_modules + 255) / 256;
-    if (validate) SPV_LAUNCH("k_id_popcount", st, k_id_popcount<<<nsm * 4, 256, 0, st>>>(P));
-    SPV_LAUNCH("k_finalize", st, k_finalize<<<nb, 256, 0, st>>>(P));
-    if (validate) SPV_LAUNCH("k_fixup", st, k_fixup<<<64, FIX_NT, 0, st>>>(P));
-    return cudaPeekAtLastError() == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;
+    // one round of the kernels; with speculation a second round follows
+    // whose kernels return at once unless a tile's entry guess failed, and
+    // otherwise redo the batch without guesses
+    auto round = [&](int rerun) -> int {
+        P.rerun = rerun;
+        P.spec = (!rerun && !c.per_module) ? c.spec : 0;
+        SPV_LAUNCH("k_prepass_mod", st, k_prepass_mod<<<nsm * 4, 256, 0, st>>>(P, c.T));
+        SPV_LAUNCH("k_prepass_scan", st, k_prepass_scan<<<1, 1024, 0, st>>>(P));
+        SPV_LAUNCH("k_tile_setup", st, k_tile_setup<<<nsm * 4, 256, 0, st>>>(P));
+        if (cudaPeekAtLastError() != cudaSuccess) return SPV_E_CUDA;
+        int rc;
+        if (!c.per_module) {
+            int per_sm = c.ctas_per_sm;
+            if (per_sm <= 0) { if (dispatch_occupancy(c, &per_sm)) return SPV_E_CUDA; if (per_sm < 1) per_sm = 1; }
+            P.persistent = 1;
+            rc = dispatch_tile(P, c, nsm * per_sm, st);
+        } else {
+            P.persistent = 0;
+            rc = 0;
+            for (int m = 0; m < batch->n_modules && !rc; m++) {
+                long long len = off[m + 1] - off[m];
+                long long ph = word_phase(batch->words, off[m]);
+                long long nt = len > 0 ? (len + ph + c.T - 1) / c.T : 1;
+                rc = dispatch_tile(P, c, (int)nt, st);
+            }
+        }
+        if (rc) return rc;
+        int nb = (batch->n_modules + 255) / 256;
+        if (validate) SPV_LAUNCH("k_id_popcount", st, k_id_popcount<<<nsm * 4, 256, 0, st>>>(P));
+        SPV_LAUNCH("k_finalize", st, k_finalize<<<nb, 256, 0, st>>>(P));
+        if (validate) SPV_LAUNCH("k_fixup", st, k_fixup<<<64, FIX_NT, 0, st>>>(P));
+        return cudaPeekAtLastError() == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;
+    };
+    int rc = round(0);
+    if (rc == SPV_SUCCESS && P.spec) rc = round(1);
+    return rc;
 }
 
 // The tile shapes k_tile is built for, tried by the autotuner.

@@ -50,7 +50,7 @@ struct Ctrl {                        // one per call, at the start of the worksp
     unsigned long long arena_used;   // words of the id-bitmap arena the batch needs
     unsigned long long total_rows;   // rows of the whole batch (written by the last tile)
     unsigned int n_fix;              // modules queued for the exact fixup pass
-    unsigned int pad;
+    unsigned int spec_failed;        // a tile's guessed entry was not its predecessor's exit: redo the call
 };
 
 struct ModState {                    // one per module

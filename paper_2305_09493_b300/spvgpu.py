@@ -43,7 +43,8 @@ class SpvTable(ctypes.Structure):
 
 class SpvConfig(ctypes.Structure):
     _fields_ = [("tile_words", ctypes.c_int32), ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("per_module", ctypes.c_int32), ("max_spins", ctypes.c_int64), ("test_stall_tile", ctypes.c_int64)]
+                ("per_module", ctypes.c_int32), ("max_spins", ctypes.c_int64), ("test_stall_tile", ctypes.c_int64),
+                ("no_speculation", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class SpvOplist(ctypes.Structure):
@@ -209,8 +210,9 @@ def _check(rc, what):
         raise SpvError(f"{what} failed with code {rc}")
 
 
-def make_config(tile_words=0, threads=0, ctas_per_sm=0, per_module=0, max_spins=0, test_stall_tile=0):
-    return SpvConfig(tile_words, threads, ctas_per_sm, per_module, max_spins, test_stall_tile)
+def make_config(tile_words=0, threads=0, ctas_per_sm=0, per_module=0, max_spins=0, test_stall_tile=0,
+                no_speculation=0):
+    return SpvConfig(tile_words, threads, ctas_per_sm, per_module, max_spins, test_stall_tile, no_speculation, 0)
 
 
 class Table:

@@ -130,6 +130,33 @@ def test_word_buffer_off_a_16_byte_boundary(gpu, shift):
         assert np.array_equal(r["out"].cpu().numpy().view(np.uint32), oracle.encode(w, off, d, True))
 
 
+def test_entry_guesses_and_their_redo_match_the_oracle(gpu):
+    """Tiles after a module's first take their first guessed instruction start
+    as their entry and check it against the predecessor's exit afterwards; a
+    framing error (a zero word count or an overrunning word count) early in a
+    long module makes the later tiles' guesses wrong, and the call redoes the
+    batch without guesses. Either way, and with guessing off, the results are
+    the oracle's."""
+    n_instr, n_k = synth.batch_shape(24, 31, median=8000, lo=2000, hi=40000)
+    w, off = synth.batch(n_instr, n_k, 31)
+    w = w.copy()
+    rng = np.random.default_rng(8)
+    for m in range(0, 24, 3):
+        lo, hi = int(off[m]) + 5, int(off[m + 1])
+        starts = oracle.decode(w[off[m]:off[m + 1]], np.array([0, hi - lo + 5], np.int64))["off"]
+        p = int(off[m]) + int(starts[len(starts) // 8])
+        w[p] = (w[p] & 0xffff) | ((0 if m % 2 else 0xfff0) << 16)    # zero word count / overrun
+    for cfg in (None, gpu.make_config(no_speculation=1), gpu.make_config(tile_words=2048, threads=128)):
+        check(gpu, w, off, cfg=cfg)
+    n_instr, n_k = synth.batch_shape(30, 33, median=6000, lo=2000, hi=30000)
+    w2, off2 = synth.batch(n_instr, n_k, 33)
+    a = run(gpu, w2, off2)
+    b = run(gpu, w2, off2, cfg=gpu.make_config(no_speculation=1))
+    assert np.array_equal(a["status"], b["status"]) and np.array_equal(a["out"], b["out"])
+    for k in ("op", "wc", "off", "rtype", "rid", "mod", "first_row", "n_instr"):
+        assert np.array_equal(a["table"][k], b["table"][k]), k
+
+
 def test_per_module_path_matches(gpu):
     n_instr, n_k = synth.batch_shape(40, 5, median=2000, lo=200, hi=20000)
     w, off = synth.batch(n_instr, n_k, 5)
