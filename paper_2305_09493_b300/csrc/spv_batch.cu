@@ -84,12 +84,12 @@ struct Params {
     int tile_words;                // words per tile of k_tile
     int out_vec;                   // out and words share their 16-byte phase: 16-byte stores
     int spec;                      // tiles may take their first guessed start as their entry
-    int rerun;                     // the second round: every kernel returns unless a guess failed
+    int rerun;                     // the redo pass: every kernel returns unless a guess failed
 };
 
-// a kernel of the second round has nothing to do unless the first round's
-// entry guesses failed somewhere
-__device__ __forceinline__ bool skip_round(const Params &P) { return P.rerun && !P.ctrl->spec_failed; }
+// a kernel of the redo pass has nothing to do unless the first pass's entry
+// guesses failed somewhere
+__device__ __forceinline__ bool skip_pass(const Params &P) { return P.rerun && !P.ctrl->spec_failed; }
 
 // words from the 16-byte boundary below word o of the batch to that word
 __host__ __device__ inline uint32_t word_phase(const uint32_t *words, long long o)
@@ -104,7 +104,7 @@ __host__ __device__ inline uint32_t word_phase(const uint32_t *words, long long 
 // ---------------------------------------------------------------------------
 __global__ void k_prepass_mod(Params P, int tile_words)
 {
-    if (skip_round(P)) return;
+    if (skip_pass(P)) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long mm = blockIdx.x * (long long)blockDim.x + threadIdx.x; mm < P.n_modules; mm += stride) {
         const int m = (int)mm;
@@ -136,7 +136,7 @@ __global__ void k_prepass_mod(Params P, int tile_words)
 
 __global__ void __launch_bounds__(1024) k_prepass_scan(Params P)
 {
-    if (skip_round(P)) return;
+    if (skip_pass(P)) return;
     __shared__ unsigned long long s_tiles[32], s_arena[32];
     __shared__ unsigned long long s_base_tiles, s_base_arena;
     int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(1024) k_prepass_scan(Params P)
 // look-back states and map entries (0: not written); clears the id arena
 __global__ void k_tile_setup(Params P)
 {
-    if (skip_round(P)) return;
+    if (skip_pass(P)) return;
     unsigned long long nt = P.ctrl->n_tiles;
     long long stride = (long long)gridDim.x * blockDim.x;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < (long long)nt; g += stride) {
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int lo = tid * L;
     const spvt::Tables &TB = g_spv_tables;
-    if (skip_round(P)) return;
+    if (skip_pass(P)) return;
 
     // per-opcode tables, once per CTA
     for (int o = tid; o < 257; o += NT) {
@@ -1041,7 +1041,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
 // ---------------------------------------------------------------------------
 __global__ void k_id_popcount(Params P)
 {
-    if (skip_round(P)) return;
+    if (skip_pass(P)) return;
     const long long aw = (long long)P.ctrl->arena_used;
     const int CH = 64;
     const long long nch = (aw + CH - 1) / CH;
@@ -1094,7 +1094,7 @@ __device__ void module_status(const Params &P, int m, unsigned long long key, ui
 
 __global__ void k_finalize(Params P)
 {
-    if (skip_round(P)) return;
+    if (skip_pass(P)) return;
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= P.n_modules) return;
     if (!P.table_mode) {
@@ -1140,7 +1140,7 @@ constexpr int FIX_HASH = 4096;
 
 __global__ void __launch_bounds__(FIX_NT) k_fixup(Params P)
 {
-    if (skip_round(P)) return;
+    if (skip_pass(P)) return;
     __shared__ unsigned long long s_best;
     __shared__ uint32_t h_key[FIX_HASH];
     __shared__ uint32_t h_min[FIX_HASH];
@@ -1536,10 +1536,10 @@ extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint3
             cudaStreamSynchronize(st) != cudaSuccess)
             return SPV_E_CUDA;
     }
-    // one round of the kernels; with speculation a second round follows
-    // whose kernels return at once unless a tile's entry guess failed, and
+    // one pass of the kernels; with speculation a redo pass follows whose
+    // kernels return at once unless a tile's entry guess failed, and
     // otherwise redo the batch without guesses
-    auto round = [&](int rerun) -> int {
+    auto pass = [&](int rerun) -> int {
         P.rerun = rerun;
         P.spec = (!rerun && !c.per_module) ? c.spec : 0;
         SPV_LAUNCH("k_prepass_mod", st, k_prepass_mod<<<nsm * 4, 256, 0, st>>>(P, c.T));
@@ -1569,8 +1569,8 @@ extern "C" int spv_process_batch(const spv_batch *batch, spv_table *table, uint3
         if (validate) SPV_LAUNCH("k_fixup", st, k_fixup<<<64, FIX_NT, 0, st>>>(P));
         return cudaPeekAtLastError() == cudaSuccess ? SPV_SUCCESS : SPV_E_CUDA;
     };
-    int rc = round(0);
-    if (rc == SPV_SUCCESS && P.spec) rc = round(1);
+    int rc = pass(0);
+    if (rc == SPV_SUCCESS && P.spec) rc = pass(1);
     return rc;
 }
 
