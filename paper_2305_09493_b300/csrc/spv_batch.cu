@@ -854,6 +854,52 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
         const uint32_t bound = P.ms[m].bound;
         const long long arena_off = P.ms[m].arena_off;
         const uint32_t id_slots = P.ms[m].id_slots;
+        uint32_t acc_lo = 0, acc_hi = 0, acc_ins = 0;  // this lane's requirements and insertions
+        // the full operand walk of row r (forms with strings, value enums and
+        // their parameters; rows that validation counts or measures; rows
+        // reaching past the tile or longer than 32 words)
+        auto full_walk = [&](unsigned r) {
+            const uint32_t p = S16[r];
+            const uint32_t w0 = ws[pwu<L>(p)];
+            const uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
+            const spvt::OpDesc &d = TB.ops[op];          // a known opcode (< 256)
+            auto iw = [&](uint32_t q) -> uint32_t {
+                const uint32_t a = p + q;
+                return a < (uint32_t)TH ? ws[pwu<L>(a)] : __ldg(src + a);
+            };
+            auto sw = [&](uint32_t q) -> uint32_t { return ws[pwu<L>(p + q)]; };
+            uint32_t ri = 0;
+            if (d.flags & 4) {
+                const uint32_t q = (d.flags & 2) ? 2u : 1u;
+                if (q < wc) ri = sw(q);
+            }
+            if (d.flags & 8) {            // the few opcodes validation counts or measures
+                if (op == 17) { atomicAdd(&s.n_cap, 1u); if (wc >= 2) { uint32_t c = iw(1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); } }
+                else if (op == 14) atomicAdd(&s.n_mm, 1u);
+                else if (op == 15) atomicAdd(&s.n_ep, 1u);
+                else if (op == 54) atomicAdd(&s.n_fn, 1u);
+            }
+            // an instruction wholly inside the staged words (almost every one)
+            // reads them without the per-word range check
+            const Walk wk = p + wc <= (uint32_t)TH ? walk_instruction(sw, wc, d, bound)
+                                                   : walk_instruction(iw, wc, d, bound);
+            if (!wk.ok) atomicMin(&s.err_key, make_key(r, R_BADOP, 0));
+            else if (wk.oob) atomicMin(&s.err_key, make_key(r, R_OOB, 0));
+            else {
+                if ((d.flags & 4) && arena_off >= 0) {
+                    if (id_slots == 0) {
+                        atomicOr(&P.arena[arena_off + (ri >> 5)], 1u << (ri & 31));
+                        acc_ins++;
+                    } else if (idset_insert(P.arena + arena_off, id_slots, ri)) {
+                        atomicOr(&s.flags, MF_DUP);
+                    }
+                }
+                uint64_t req = wk.req;
+                if (d.flags & 8) req |= width_caps(iw, op, wc);
+                acc_lo |= (uint32_t)req;
+                acc_hi |= (uint32_t)(req >> 32);
+            }
+        };
         if (P.validate) {
             // rows in chunks of 32 from a shared counter: warp 0 joins when
             // its look-back is done. A row in the fast operand form (fixed ids
@@ -897,70 +943,32 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
                 if ((have && !known) || (fastrow && !ok) || oob)
                     atomicMin(&s.err_key, make_key(r, !known ? R_UNKNOWN : (!ok ? R_BADOP : R_OOB), 0));
                 const bool good = ok && !oob;
-                uint32_t req_lo = 0, req_hi = 0, inserted = 0;
                 const int cap = (int)(int8_t)((fdv.y >> 8) & 0xffu);
-                if (good && cap >= 0) { if (cap < 32) req_lo = 1u << cap; else req_hi = 1u << (cap - 32); }
+                if (good && cap >= 0) { if (cap < 32) acc_lo |= 1u << cap; else acc_hi |= 1u << (cap - 32); }
                 if (good && (flags & 4u) && arena_off >= 0) {
                     const uint32_t ri = ws[pwu<L>(p + ((flags & 2u) ? 2u : 1u))];
                     if (id_slots == 0) {
                         // no wait on the old value: duplicates show up later as
                         // fewer bits set than ids inserted
                         atomicOr(&P.arena[arena_off + (ri >> 5)], 1u << (ri & 31));
-                        inserted = 1;
+                        acc_ins++;
                     } else if (idset_insert(P.arena + arena_off, id_slots, ri)) {
                         atomicOr(&s.flags, MF_DUP);
                     }
                 }
-                // the rest: the full operand walk (forms with strings, value
-                // enums and their parameters; rows that validation counts or
-                // measures; rows reaching past the tile or longer than 32 words)
-                if (__any_sync(FULL, known && !fastrow) && known && !fastrow) {
-                    const spvt::OpDesc &d = TB.ops[op];          // a known opcode (< 256)
-                    auto iw = [&](uint32_t q) -> uint32_t {
-                        const uint32_t a = p + q;
-                        return a < (uint32_t)TH ? ws[pwu<L>(a)] : __ldg(src + a);
-                    };
-                    auto sw = [&](uint32_t q) -> uint32_t { return ws[pwu<L>(p + q)]; };
-                    uint32_t ri = 0;
-                    if (d.flags & 4) {
-                        const uint32_t q = (d.flags & 2) ? 2u : 1u;
-                        if (q < wc) ri = sw(q);
-                    }
-                    if (d.flags & 8) {            // the few opcodes validation counts or measures
-                        if (op == 17) { atomicAdd(&s.n_cap, 1u); if (wc >= 2) { uint32_t c = iw(1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); } }
-                        else if (op == 14) atomicAdd(&s.n_mm, 1u);
-                        else if (op == 15) atomicAdd(&s.n_ep, 1u);
-                        else if (op == 54) atomicAdd(&s.n_fn, 1u);
-                    }
-                    // an instruction wholly inside the staged words (almost every one)
-                    // reads them without the per-word range check
-                    const Walk wk = p + wc <= (uint32_t)TH ? walk_instruction(sw, wc, d, bound)
-                                                           : walk_instruction(iw, wc, d, bound);
-                    if (!wk.ok) atomicMin(&s.err_key, make_key(r, R_BADOP, 0));
-                    else if (wk.oob) atomicMin(&s.err_key, make_key(r, R_OOB, 0));
-                    else {
-                        if ((d.flags & 4) && arena_off >= 0) {
-                            if (id_slots == 0) {
-                                atomicOr(&P.arena[arena_off + (ri >> 5)], 1u << (ri & 31));
-                                inserted = 1;
-                            } else if (idset_insert(P.arena + arena_off, id_slots, ri)) {
-                                atomicOr(&s.flags, MF_DUP);
-                            }
-                        }
-                        uint64_t req = wk.req;
-                        if (d.flags & 8) req |= width_caps(iw, op, wc);
-                        req_lo = (uint32_t)req;
-                        req_hi = (uint32_t)(req >> 32);
-                    }
-                }
-                const uint32_t rlo = __reduce_or_sync(FULL, req_lo);
-                const uint32_t rhi = __reduce_or_sync(FULL, req_hi);
-                const uint32_t nins = __reduce_add_sync(FULL, inserted);
-                if (lane == 0) {
-                    if (rlo) atomicOr(&s.req_lo, rlo);
-                    if (rhi) atomicOr(&s.req_hi, rhi);
-                    if (nins) atomicAdd(&s.n_ids, nins);
-                }
+                // the rest take the full operand walk, here, while warp 0 may
+                // still be waiting on its look-back
+                const bool slow = known && !fastrow;
+                if (__any_sync(FULL, slow) && slow) full_walk(r);
+            }
+            // this warp's requirements and insertions, once for all its chunks
+            const uint32_t rlo = __reduce_or_sync(FULL, acc_lo);
+            const uint32_t rhi = __reduce_or_sync(FULL, acc_hi);
+            const uint32_t nins = __reduce_add_sync(FULL, acc_ins);
+            if (lane == 0) {
+                if (rlo) atomicOr(&s.req_lo, rlo);
+                if (rhi) atomicOr(&s.req_hi, rhi);
+                if (nins) atomicAdd(&s.n_ids, nins);
             }
         }
         __syncthreads();
@@ -996,6 +1004,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
             rmax = __reduce_max_sync(FULL, rmax);
             if (lane == 0 && rmax) atomicMax(&s.max_rid, rmax);
         }
+
         __syncthreads();
         // the entry guess of a speculating tile against its predecessor's exit
         if (spec_tile && tid == 0) {
