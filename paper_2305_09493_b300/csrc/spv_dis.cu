@@ -744,6 +744,7 @@ struct MainSmem {
     unsigned long long base;
     int m0, nm;
     int gave_up;
+    unsigned int fnext;             // next chunk of items to format
 };
 
 // ---------------------------------------------------------------------------
@@ -1008,6 +1009,7 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
             if (lane == 0) {
                 s.tile = tt;
                 s.gave_up = 0;
+                s.fnext = 0;
                 s.wlo = ~0ull;
                 s.whi = 0;
             }
@@ -1199,9 +1201,19 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
         __syncthreads();                              // every item's offset (and an oversized tile's base)
         // 4. format once, in shape order, into shared memory; then the offset
         if (staged) {
+            // warp 0 looks back for the tile's offset first, while the other
+            // warps format: items go out 32 at a time (in shape order) from a
+            // shared counter, and warp 0 joins when its look-back is done
+            if (wid == 0) dis_lookback(P, s, t, total, lane, last_tile);
             if (P.text_cap > 0) {
-                for (int q = tid; q < ITEMS; q += DNT) {
-                    int j = s.perm[q];
+                for (;;) {
+                    unsigned cb = 0;
+                    if (lane == 0) cb = atomicAdd(&s.fnext, 32u);
+                    cb = __shfl_sync(0xffffffffu, cb, 0);
+                    if (cb >= (unsigned)ITEMS) break;
+                    const int q = (int)cb + lane;
+                    if (q >= ITEMS) continue;
+                    const int j = s.perm[q];
                     if (s.im[j] < 0 || s.ilen[j] == 0) continue;
                     if (s.iok[j] == 2) {
                         RowCtx c;
@@ -1213,7 +1225,6 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
                     }
                 }
             }
-            if (wid == 0) dis_lookback(P, s, t, total, lane, last_tile);
             __syncthreads();
         }
         const unsigned long long base = s.base;
