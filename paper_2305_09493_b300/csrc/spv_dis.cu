@@ -997,12 +997,8 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
     const long long n_items = (long long)P.ctrl->n_items;
     const long long ntiles = (n_items + ITEMS - 1) / ITEMS;
     init_text_tables(s);
-    // a ticket is taken when its tile starts: a tile waits only on lower
-    // tiles, whose holders are running, so the look-backs always end; a
-    // ticket taken a tile ahead would hold back every later tile's look-back
-    for (;;) {
-        // warp 0: the tile, its modules and their first items
-        if (wid == 0) {
+    // warp 0: take the next tile's ticket; its modules and their first items
+    auto setup_tile = [&]() {
             unsigned int ticket = 0;
             if (lane == 0) ticket = atomicAdd(&P.ctrl->next_tile, 1u);
             const long long tt = (long long)__shfl_sync(0xffffffffu, ticket, 0);
@@ -1031,7 +1027,16 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
                     mc.bloom = md.bloom; mc.arena_off = md.arena_off; mc.first = P.first_row[m0 + lane];
                 }
             }
-        }
+            };
+    bool prefetched = false;          // warp 0 set up the next tile already
+    // a ticket is taken when its tile starts: a tile waits only on lower
+    // tiles, whose holders are running, so the look-backs always end; a
+    // ticket taken a tile ahead would hold back every later tile's look-back
+    for (;;) {
+        // warp 0: the tile, its modules and their first items (done already
+        // when it was set up during the last tile's copy-out)
+        if (wid == 0 && !prefetched) setup_tile();
+        prefetched = false;
         if (tid < NSHAPE) s.cls_n[tid] = 0;
         __syncthreads();
         const long long t = s.tile;
@@ -1231,6 +1236,10 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
         for (int j = tid; j < ITEMS; j += DNT)
             if (s.im[j] >= 0 && s.ihdr[j]) P.text_off[s.im[j]] = base + s.ioff[j];
         const bool write = !s.gave_up && base + total <= P.text_cap;
+        // a tile formatted in one window: warp 0 sets up the next tile while
+        // the other warps copy this one out
+        if (staged && wid == 0) { setup_tile(); prefetched = true; }
+        const int ct = staged ? tid - 32 : tid, cs = staged ? DNT - 32 : DNT;
         // 5. copy out, window by window of TEXT_SMEM bytes: a tile with more
         //    text formats each window in turn (a line crossing a window edge
         //    is formatted once per window it touches, clipped to it)
@@ -1262,21 +1271,23 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
                 auto gword = [&](uint32_t k) -> uint32_t {   // k = w - w0 (>= 1 when sh != 0)
                     return sh == 0 ? sw[k] : __funnelshift_r(sw[k - 1], sw[k], 8 * (4 - sh));
                 };
-                if ((((uintptr_t)P.text) & 15) == 0) {
+                if (staged && wid == 0) {
+                    // setting up the next tile
+                } else if ((((uintptr_t)P.text) & 15) == 0) {
                     const unsigned long long c0 = (g0 + 15) >> 4, c1 = g1 >> 4;   // whole chunks [c0, c1)
                     uint4 *t4 = reinterpret_cast<uint4 *>(P.text);
-                    for (unsigned long long c = c0 + tid; c < c1; c += DNT) {
+                    for (unsigned long long c = c0 + ct; c < c1; c += cs) {
                         const uint32_t k = (uint32_t)((c << 2) - w0);
                         t4[c] = make_uint4(gword(k), gword(k + 1), gword(k + 2), gword(k + 3));
                     }
                     const unsigned long long h1 = (c0 << 4) < g1 ? (c0 << 4) : g1;
-                    for (unsigned long long g = g0 + tid; g < h1; g += DNT) P.text[g] = s.text[g - g0];
+                    for (unsigned long long g = g0 + ct; g < h1; g += cs) P.text[g] = s.text[g - g0];
                     if (c1 >= c0)
-                        for (unsigned long long g = (c1 << 4) + tid; g < g1; g += DNT) P.text[g] = s.text[g - g0];
+                        for (unsigned long long g = (c1 << 4) + ct; g < g1; g += cs) P.text[g] = s.text[g - g0];
                 } else {
                     const bool aligned = (((uintptr_t)P.text) & 3) == 0;
                     uint32_t *tw = reinterpret_cast<uint32_t *>(P.text);
-                    for (unsigned long long w = w0 + tid; w < w1; w += DNT) {
+                    for (unsigned long long w = w0 + ct; w < w1; w += cs) {
                         unsigned long long gb = w << 2;
                         if (aligned && gb >= g0 && gb + 4 <= g1) {
                             tw[w] = gword((uint32_t)(w - w0));
