@@ -466,24 +466,78 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
         // the guess is a chain when the successor marks are exactly the
         // candidates but one (the first), each mark made once, and exactly
         // one candidate leaves the tile
-        if (live) {
-            uint32_t prev = __shfl_up_sync(FULL, sl, 1);
-            if (lane == 0) prev = wid ? s.sl_hi[wid - 1] : 0u;
-            const uint32_t succ = (sl & SEGM) | (prev >> L) | ((s.far[lo >> 5] >> (lo & 31)) & SEGM);
-            uint32_t r1 = (uint32_t)__popc(X & ~succ) | ((uint32_t)__popc(succ & ~X) << 16);
-            uint32_t r2 = ne | ((uint32_t)__popc(X) << 16);
-            r1 = __reduce_add_sync(FULL, r1);
-            r2 = __reduce_add_sync(FULL, r2);
-            if (lane == 0) { atomicAdd(&s.cnt1, r1); atomicAdd(&s.cnt2, r2); }
-            if (X) atomicMin(&s.xfirst, (uint32_t)(lo + __ffs(X) - 1));
+        uint32_t succ = 0;
+        auto chain_test = [&]() {
+            if (live) {
+                uint32_t prev = __shfl_up_sync(FULL, sl, 1);
+                if (lane == 0) prev = wid ? s.sl_hi[wid - 1] : 0u;
+                succ = (sl & SEGM) | (prev >> L) | ((s.far[lo >> 5] >> (lo & 31)) & SEGM);
+                uint32_t r1 = (uint32_t)__popc(X & ~succ) | ((uint32_t)__popc(succ & ~X) << 16);
+                uint32_t r2 = ne | ((uint32_t)__popc(X) << 16);
+                r1 = __reduce_add_sync(FULL, r1);
+                r2 = __reduce_add_sync(FULL, r2);
+                if (lane == 0) { atomicAdd(&s.cnt1, r1); atomicAdd(&s.cnt2, r2); }
+                if (X) atomicMin(&s.xfirst, (uint32_t)(lo + __ffs(X) - 1));
+            }
+            __syncthreads();
+        };
+        auto is_chain = [&]() {
+            const uint32_t c1 = s.cnt1, c2 = s.cnt2;
+            const uint32_t nA = c1 & 0xffffu, nB = c1 >> 16, nE = c2 & 0xffffu, nX = c2 >> 16;
+            return live && (nX == 0 || (nA == 1 && nB == 0 && nE == 1 && s.exitX <= end_s));
+        };
+        chain_test();
+        // A module's first tile whose guess is not a chain. Its first start
+        // (word 5) is known, so no other candidate without a predecessor
+        // starts an instruction, and neither does a candidate that only such
+        // candidates lead to: a false candidate is a literal or string word
+        // that reads as an instruction, and the few words it leads to soon
+        // fall on a non-candidate, join the chain or leave the tile. They are
+        // dropped round by round, each round marking successors afresh from
+        // the remaining candidates and testing again; a tile still not a
+        // chain after the last round takes the exact path.
+        if (live && k == 0 && !is_chain()) {
+            const uint32_t e0 = ph + 5;
+            const bool e0_cand = e0 < tile_n && ((s.X[e0 / L] >> (e0 % L)) & 1u);
+            const uint32_t keep = e0 >= (uint32_t)lo && e0 < (uint32_t)(lo + L) ? 1u << (e0 - (uint32_t)lo) : 0u;
+            const int lim = (int)tile_n - lo;
+            #pragma unroll 1
+            for (int round = 0; round < 4 && e0_cand && !is_chain(); round++) {
+                __syncthreads();                       // every thread has read the counts
+                X &= succ | keep;
+                if (tid == 0) { s.cnt1 = 0; s.cnt2 = 0; s.exitX = DEAD; s.xfirst = DEAD; }
+                for (int i = tid; i < T / 32; i += NT) s.far[i] = 0u;
+                __syncthreads();
+                uint32_t ex = 0, farm = 0;
+                sl = 0; ne = 0;
+                for (uint32_t x = X; x; x &= x - 1) {
+                    const int j = __ffs(x) - 1;
+                    const int nx = j + (int)(ws[pw<L>(lo + j)] >> 16);
+                    const bool leaves = nx >= lim;
+                    ne += leaves ? 1u : 0u;
+                    ex = leaves ? (uint32_t)(lo + nx) : ex;
+                    sl |= (!leaves && nx < 2 * L) ? (1u << (nx & 31)) : 0u;
+                    farm |= (!leaves && nx >= 2 * L) ? (1u << j) : 0u;
+                }
+                while (farm) {
+                    const int j = __ffs(farm) - 1;
+                    farm &= farm - 1;
+                    const int at = lo + j + (int)(ws[pw<L>(lo + j)] >> 16);
+                    atomicOr(&s.far[at >> 5], 1u << (at & 31));
+                }
+                s.X[tid] = (uint16_t)X;
+                if (lane == 31) s.sl_hi[wid] = sl;
+                if (ne) s.exitX = ex;
+                __syncthreads();
+                chain_test();
+            }
         }
-        __syncthreads();
         const uint32_t exitX = s.exitX;
         bool fast = false, spec_tile = false;
         {
-            const uint32_t c1 = s.cnt1, c2 = s.cnt2;
-            const uint32_t nA = c1 & 0xffffu, nB = c1 >> 16, nE = c2 & 0xffffu, nX = c2 >> 16;
-            fast = live && (nX == 0 || (nA == 1 && nB == 0 && nE == 1 && exitX <= end_s));
+            const uint32_t c2 = s.cnt2;
+            const uint32_t nX = c2 >> 16;
+            fast = is_chain();
             // a later tile of its module whose guessed starts form a chain takes
             // the chain's first start as its entry: its exit and row count are
             // known now; the guess is checked against the predecessor's exit at
@@ -819,29 +873,9 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
         if (wid == 0) {
             unsigned long long excl = 0;
             if (g > 0) {
-                long long hi_j = g - 1;
-                long long spins = 0;
-                bool gave_up = false;
-                for (;;) {
-                    long long j = hi_j - lane;
-                    unsigned long long st = j >= 0 ? ld_relaxed(&P.cstate[j]) : F_EXIT;
-                    unsigned long long f = st & F_MASK;
-                    unsigned exitm = __ballot_sync(FULL, f == F_EXIT);
-                    unsigned nonem = __ballot_sync(FULL, f == 0);
-                    int le = exitm ? __ffs(exitm) - 1 : 32;
-                    unsigned below = le == 32 ? FULL : ((1u << le) - 1u);
-                    if (nonem & below) {
-                        if (++spins > P.max_spins) { gave_up = true; break; }
-                        spin_pause();
-                        continue;
-                    }
-                    unsigned long long v = (lane <= le && j >= 0) ? (st & ~F_MASK) : 0ull;
-                    #pragma unroll
-                    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
-                    excl += v;
-                    if (exitm) break;
-                    hi_j -= 32;
-                }
+                bool gave_up;
+                // 32 states a poll: the nearest inclusive state is seldom far back
+                excl = warp_lookback_sum<1>(P.cstate, g - 1, F_EXIT, F_MASK, P.max_spins, lane, gave_up);
                 if (gave_up) { excl = 0; if (lane == 0) s.timeout = 1; }
                 if (lane == 0 && !stalled) st_relaxed(&P.cstate[g], F_EXIT | (excl + tile_count));
             }

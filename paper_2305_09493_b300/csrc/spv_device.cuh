@@ -141,6 +141,61 @@ __device__ __forceinline__ void st_relaxed32(uint32_t *p, uint32_t v)
 }
 __device__ __forceinline__ void spin_pause() { __nanosleep(32); }
 
+// Decoupled look-back by one warp (all 32 lanes) over state[0 .. hi]: a state
+// is 0 (not yet published), inclusive (flag `incl`: the sum of every state up
+// to and including its own) or an aggregate (any other flag: its own count);
+// the count is the state's low 62 bits. Returns the sum of the aggregates
+// down to and including the nearest inclusive state (0 for hi < 0). Each poll
+// reads U x 32 states, all in flight at once, so a look-back that has to
+// reach far behind takes few memory round trips. A poll that finds a state
+// not yet published inside the reach is repeated; after max_spins polls the
+// warp gives up (gave_up set, the sum so far returned).
+template <int U>
+__device__ __forceinline__ unsigned long long warp_lookback_sum(const unsigned long long *state, long long hi,
+                                                                unsigned long long incl, unsigned long long mask,
+                                                                long long max_spins, int lane, bool &gave_up)
+{
+    unsigned long long excl = 0;
+    long long spins = 0;
+    gave_up = false;
+    while (hi >= 0) {
+        unsigned long long st[U];
+        #pragma unroll
+        for (int u = 0; u < U; u++) {
+            const long long j = hi - 32 * u - lane;
+            st[u] = j >= 0 ? ld_relaxed(&state[j]) : incl;     // before state 0: inclusive 0
+        }
+        int reach = 32 * U;                                    // distance of the nearest inclusive state
+        bool wait = false;
+        #pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (reach < 32 * U || wait) continue;
+            const unsigned long long f = st[u] & mask;
+            const unsigned im = __ballot_sync(0xffffffffu, f == incl);
+            const unsigned nm = __ballot_sync(0xffffffffu, f == 0);
+            const int le = im ? __ffs(im) - 1 : 32;
+            const unsigned below = le == 32 ? 0xffffffffu : ((1u << le) - 1u);
+            if (nm & below) wait = true;
+            else if (im) reach = 32 * u + le;
+        }
+        if (wait) {
+            if (++spins > max_spins) { gave_up = true; break; }
+            spin_pause();
+            continue;
+        }
+        unsigned long long v = 0;
+        #pragma unroll
+        for (int u = 0; u < U; u++)
+            if (32 * u + lane <= reach) v += st[u] & ~mask;
+        #pragma unroll
+        for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+        excl += v;
+        if (reach < 32 * U) break;
+        hi -= 32 * U;
+    }
+    return excl;
+}
+
 // ---------------- header ----------------
 // Listing 4 header: magic, version 0x00MMmm00 (major 1, minor <= 6),
 // generator, bound, schema 0.

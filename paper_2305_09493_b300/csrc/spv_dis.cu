@@ -953,28 +953,10 @@ __device__ void dis_lookback(const DP &P, MainSmem &s, long long t, uint32_t tot
 {
     unsigned long long excl = 0;
     if (t > 0) {
-        long long hi = t - 1, spins = 0;
-        bool gave_up = false;
-        for (;;) {
-            long long jj = hi - lane;
-            unsigned long long st = jj >= 0 ? ld_relaxed(&P.tstate[jj]) : F_INC;
-            unsigned long long f = st & F_MSK;
-            unsigned incm = __ballot_sync(0xffffffffu, f == F_INC);
-            unsigned nonem = __ballot_sync(0xffffffffu, f == 0);
-            int le = incm ? __ffs(incm) - 1 : 32;
-            unsigned below = le == 32 ? 0xffffffffu : ((1u << le) - 1u);
-            if (nonem & below) {
-                if (++spins > P.max_spins) { gave_up = true; break; }
-                spin_pause();
-                continue;
-            }
-            unsigned long long v2 = (lane <= le && jj >= 0) ? (st & ~F_MSK) : 0ull;
-            #pragma unroll
-            for (int d = 16; d > 0; d >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, d);
-            excl += v2;
-            if (incm) break;
-            hi -= 32;
-        }
+        bool gave_up;
+        // 128 states a poll: with one tile in flight per SM the nearest
+        // inclusive state is often a few hundred tiles back
+        excl = warp_lookback_sum<4>(P.tstate, t - 1, F_INC, F_MSK, P.max_spins, lane, gave_up);
         if (gave_up && lane == 0) { atomicExch(&P.ctrl->timeout, 1u); s.gave_up = 1; }
         if (lane == 0 && t != P.stall_tile) st_relaxed(&P.tstate[t], F_INC | (excl + total));
     }

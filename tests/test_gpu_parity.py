@@ -157,6 +157,54 @@ def test_entry_guesses_and_their_redo_match_the_oracle(gpu):
         assert np.array_equal(a["table"][k], b["table"][k]), k
 
 
+def _literal_module(pattern, n_pad, width=32):
+    """The minimal module with n_pad 32-bit constants, then one constant whose
+    literal words are `pattern` (of an integer type `width` bits wide), ahead
+    of the function."""
+    base = H.minimal_body()
+    body = list(base[:8])
+    ty = 2
+    if width != 32:
+        ty = 9
+        body.append(H.ins(H.OpTypeInt, ty, width, 0))
+    body += [H.ins(H.OpConstant, 2, 12 + i, 7) for i in range(n_pad)]
+    body.append(H.ins(H.OpConstant, ty, 10, *pattern))
+    body += base[8:]
+    return H.module(body, bound=12 + n_pad)
+
+
+def test_literals_that_read_as_instructions_in_a_first_tile(gpu):
+    """A module's first tile whose constants hold words that read as
+    instructions: a one-word OpReturn (its successor the next real start), a
+    two-word OpBranch (its successor inside the next constant), an
+    OpTypeStruct whose word count runs far past the tile, chains of two and
+    of eight such words (a 64- and a 256-bit literal), at the start of the
+    tile, inside it and at its end. The guessed starts are not a chain; the
+    false ones are dropped (or, past a few rounds, the exact path runs) and
+    every result is the oracle's."""
+    RET = (1 << 16) | H.OpReturn
+    BR = (2 << 16) | H.OpBranch
+    FAR = (0xF000 << 16) | 30                       # OpTypeStruct, 61,440 words
+    cases = [([RET], 32), ([BR], 32), ([FAR], 32), ([RET, RET], 64), ([RET] * 8, 256), ([BR, RET], 64),
+             ([RET, BR], 64)]
+    mods = []
+    for pattern, width in cases:
+        for n_pad in (0, 1, 120, 1018, 1019, 1020, 1021, 1022):
+            mods.append(_literal_module(pattern, n_pad, width))
+    # a false start in a later tile of a long module as well
+    long_body = list(H.minimal_body()[:8]) + [H.ins(H.OpConstant, 2, 12 + i, RET if i % 700 == 699 else 7)
+                                              for i in range(3000)] + list(H.minimal_body()[8:])
+    mods.append(H.module(long_body, bound=3012))
+    w, off = H.batch(mods)
+    for cfg in (None, gpu.make_config(tile_words=2048, threads=128), gpu.make_config(tile_words=512, threads=64),
+                gpu.make_config(no_speculation=1)):
+        check(gpu, w, off, cfg=cfg)
+    # the same modules one per batch (every one starts on a 16-byte boundary)
+    for mm in mods[::5]:
+        ww, oo = H.batch([mm])
+        check(gpu, ww, oo)
+
+
 def test_per_module_path_matches(gpu):
     n_instr, n_k = synth.batch_shape(40, 5, median=2000, lo=200, hi=20000)
     w, off = synth.batch(n_instr, n_k, 5)
