@@ -1,26 +1,29 @@
 // spv_batch.cu -- batched decode / validate / encode of SPIR-V modules.
 //
 // One persistent launch processes every module of a batch, split into tiles
-// of T words (a module owns ceil(len / T) tiles, at least one). Each CTA
-// claims tiles in order from an atomic counter and, per tile:
-//   1. stages the tile (+ a halo) into shared memory with coalesced loads;
+// of T words laid on 16-byte boundaries (a module owns at least one). Each
+// CTA claims tiles in order from an atomic counter and, per tile:
+//   1. stages the tile (+ a halo) into shared memory with 16-byte copies;
 //   2. finds instruction starts. Starts form a chain p -> p + wc(p) from
 //      word 5 of the module (section 3.4.6: instructions are word-counted
-//      32-bit word sequences). Each thread owns a 16-word segment and
-//      computes, backwards, for every position the first chain position past
-//      its segment (or "dead"); each warp then walks 32 candidate entries
-//      through its 512 words; warp 0 composes the warp maps into the tile's
-//      map for 32 candidate entry positions and publishes it. The tile's true
-//      entry comes from a decoupled look-back: the nearest predecessor that
-//      has published its exit, then the predecessors' maps applied in order.
-//      Waits are bounded (max_spins) and end in SPV_TIMEOUT, never a hang.
-//   3. marks starts per segment, counts them and gets the tile's global row
-//      base from a second decoupled look-back (sum of predecessors' counts);
-//   4. writes one structure-of-arrays row per instruction and validates it
+//      32-bit word sequences). Every word whose opcode and word count could
+//      start an instruction is a guessed start; the guess is the chain when
+//      each guessed start but one is the successor of exactly one other and
+//      exactly one leaves the tile. A module's first tile drops false guesses
+//      (literals that read as instructions) round by round from its known
+//      entry; a later tile takes its first guessed start as its entry,
+//      publishes its exit and row count at once and checks the entry against
+//      its predecessor's exit at the end (a wrong guess redoes the batch
+//      without guesses). A tile whose guess is not a chain takes the exact
+//      path: per-segment exits, warp maps, the tile map, and its entry from a
+//      decoupled look-back over the predecessors' exits and maps. Waits are
+//      bounded (max_spins) and end in SPV_TIMEOUT, never a hang;
+//   3. re-encodes the staged words (fused path) and validates the rows
 //      (section 3.4.5 rules; ids below the bound and each result id set once,
-//      section 3.4.2) into per-tile aggregates.
-// The tile is re-encoded from its staged words by the other warps while
-// warp 0 runs the first look-back.
+//      section 3.4.2) into per-tile aggregates, in chunks of 32 rows;
+//   4. gets the tile's global first row from a second decoupled look-back
+//      (sum of predecessors' counts) and writes one structure-of-arrays row
+//      per instruction.
 // A prepass reads headers and lays out tiles and id bitmaps; a finalize pass
 // turns per-module aggregates into status codes; an exact fixup pass runs
 // only for modules with a duplicate result id or a missing capability.
@@ -867,24 +870,6 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
             while (x) { int b = __ffs(x) - 1; x &= x - 1; S16[o++] = (uint16_t)(lo + b); }
         }
         __syncthreads();
-        // warp 0: the tile's first row (decoupled look-back over all tiles'
-        // counts); meanwhile the other warps validate the tile's rows, which
-        // needs no global row index, and warp 0 joins them after
-        if (wid == 0) {
-            unsigned long long excl = 0;
-            if (g > 0) {
-                bool gave_up;
-                // 32 states a poll: the nearest inclusive state is seldom far back
-                excl = warp_lookback_sum<1>(P.cstate, g - 1, F_EXIT, F_MASK, P.max_spins, lane, gave_up);
-                if (gave_up) { excl = 0; if (lane == 0) s.timeout = 1; }
-                if (lane == 0 && !stalled) st_relaxed(&P.cstate[g], F_EXIT | (excl + tile_count));
-            }
-            if (lane == 0) {
-                s.row_base = excl;
-                if (k == 0) P.first_row[m] = (int64_t)excl;
-                if (g == n_tiles - 1) P.ctrl->total_rows = excl + tile_count;
-            }
-        }
         const uint32_t bound = P.ms[m].bound;
         const long long arena_off = P.ms[m].arena_off;
         const uint32_t id_slots = P.ms[m].id_slots;
@@ -935,8 +920,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
             }
         };
         if (P.validate) {
-            // rows in chunks of 32 from a shared counter: warp 0 joins when
-            // its look-back is done. A row in the fast operand form (fixed ids
+            // rows in chunks of 32 from a shared counter. A row in the fast operand form (fixed ids
             // and literals, then a plain tail or one bit-enum word; wholly in
             // the tile, at most 32 words) is checked here, in the order of
             // section 3.4.5's checks: known opcode, its word count against the
@@ -990,8 +974,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
                         atomicOr(&s.flags, MF_DUP);
                     }
                 }
-                // the rest take the full operand walk, here, while warp 0 may
-                // still be waiting on its look-back
+                // the rest take the full operand walk, in the same chunk
                 const bool slow = known && !fastrow;
                 if (__any_sync(FULL, slow) && slow) full_walk(r);
             }
@@ -1003,6 +986,25 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
                 if (rlo) atomicOr(&s.req_lo, rlo);
                 if (rhi) atomicOr(&s.req_hi, rhi);
                 if (nins) atomicAdd(&s.n_ids, nins);
+            }
+        }
+        // warp 0: the tile's first row (decoupled look-back over all tiles'
+        // counts), after its share of the validation (which needs no global
+        // row index): by then the predecessors' counts are mostly published,
+        // and a warp that waits sleeps longer between polls
+        if (wid == 0) {
+            unsigned long long excl = 0;
+            if (g > 0) {
+                bool gave_up;
+                // 32 states a poll: the nearest inclusive state is seldom far back
+                excl = warp_lookback_sum<1, 512>(P.cstate, g - 1, F_EXIT, F_MASK, P.max_spins, lane, gave_up);
+                if (gave_up) { excl = 0; if (lane == 0) s.timeout = 1; }
+                if (lane == 0 && !stalled) st_relaxed(&P.cstate[g], F_EXIT | (excl + tile_count));
+            }
+            if (lane == 0) {
+                s.row_base = excl;
+                if (k == 0) P.first_row[m] = (int64_t)excl;
+                if (g == n_tiles - 1) P.ctrl->total_rows = excl + tile_count;
             }
         }
         __syncthreads();

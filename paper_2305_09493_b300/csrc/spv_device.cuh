@@ -148,15 +148,17 @@ __device__ __forceinline__ void spin_pause() { __nanosleep(32); }
 // down to and including the nearest inclusive state (0 for hi < 0). Each poll
 // reads U x 32 states, all in flight at once, so a look-back that has to
 // reach far behind takes few memory round trips. A poll that finds a state
-// not yet published inside the reach is repeated; after max_spins polls the
-// warp gives up (gave_up set, the sum so far returned).
-template <int U>
+// not yet published inside the reach is repeated, after a pause that starts
+// at 32 ns and doubles up to max_ns; after max_spins polls the warp gives up
+// (gave_up set, the sum so far returned).
+template <int U, unsigned max_ns = 32>
 __device__ __forceinline__ unsigned long long warp_lookback_sum(const unsigned long long *state, long long hi,
                                                                 unsigned long long incl, unsigned long long mask,
                                                                 long long max_spins, int lane, bool &gave_up)
 {
     unsigned long long excl = 0;
     long long spins = 0;
+    unsigned ns = 32;
     gave_up = false;
     while (hi >= 0) {
         unsigned long long st[U];
@@ -180,7 +182,8 @@ __device__ __forceinline__ unsigned long long warp_lookback_sum(const unsigned l
         }
         if (wait) {
             if (++spins > max_spins) { gave_up = true; break; }
-            spin_pause();
+            __nanosleep(ns);
+            ns = ns < max_ns ? 2 * ns : max_ns;
             continue;
         }
         unsigned long long v = 0;
