@@ -745,6 +745,7 @@ struct MainSmem {
     int m0, nm;
     int gave_up;
     unsigned int fnext;             // next chunk of items to format
+    unsigned int mnext;             // next chunk of items to measure
 };
 
 // ---------------------------------------------------------------------------
@@ -988,6 +989,7 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
                 s.tile = tt;
                 s.gave_up = 0;
                 s.fnext = 0;
+                s.mnext = 0;
                 s.wlo = ~0ull;
                 s.whi = 0;
             }
@@ -1130,8 +1132,17 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
         for (int j = tid; j < ITEMS; j += DNT) s.perm[s.cls_n[s.icls[j]] + s.rank[j]] = (uint16_t)j;
         __syncthreads();
 
-        // 2. measure, in shape order
-        for (int q = tid; q < ITEMS; q += DNT) {
+        // 2. measure, in shape order, 32 items at a time from a shared
+        //    counter: the few shapes without the fast line form (a module's
+        //    preamble) come first, and their long formatting overlaps the
+        //    other warps' chunks
+        for (;;) {
+            unsigned cb = 0;
+            if (lane == 0) cb = atomicAdd(&s.mnext, 32u);
+            cb = __shfl_sync(0xffffffffu, cb, 0);
+            if (cb >= (unsigned)ITEMS) break;
+            const int q = (int)cb + lane;
+            if (q >= ITEMS) continue;
             int j = s.perm[q];
             int m = s.im[j];
             uint32_t len = 0;
