@@ -256,6 +256,36 @@ template <int L> __device__ __forceinline__ int pw(int i) { return i + 4 * (i / 
 template <int L> __device__ __forceinline__ uint32_t pwu(uint32_t i) { return i + 4u * (i / L); }
 template <int L> __device__ __forceinline__ int pe(int i) { return i + i / L; }         // exit-array index
 
+// What validating one row needs of its opcode, in two words.
+//   x: the word positions that hold ids when the row has 32 words (the fixed
+//      ids, then every position of an id tail); a row of wc words takes the
+//      low wc bits
+//   y: bits 0-4 need (1 + fixed operand words); bits 5-10 r: the words past
+//      them, d = wc - need, are valid for d < r (1: none, 32: any tail, 0:
+//      only a bit-enum word with its parameters); bit 11 d must be even (id
+//      pairs); bit 12 the tail is one bit-enum word (d = 1 + its parameters
+//      is valid); bits 13-14 its bit-enum kind; bit 15 the fast form applies
+//      (known, fixed ids / literals and a plain tail, not counted by
+//      validation); bit 16 known; bit 17 has a result id; bit 18 has a
+//      result type (the result id is word 2, else word 1); bits 24-31 the
+//      required capability (int8, -1 none)
+__host__ __device__ inline uint2 vdesc(const spvt::OpDesc &d)
+{
+    if (!(d.flags & 1)) return make_uint2(0u, 0u);
+    uint32_t x = 0, y = (1u << 16) | ((uint32_t)(uint8_t)d.cap << 24);
+    if (d.flags & 4) y |= 1u << 17;
+    if (d.flags & 2) y |= 1u << 18;
+    if ((d.fast & 1) && !(d.flags & 8)) {
+        const uint32_t need = 1u + d.nfixed, tail = (d.fast >> 1) & 7u;
+        x = d.id_mask;
+        if (tail == 1 || tail == 3) x |= 0xffffffffu << need;
+        const uint32_t r = tail == 0 ? 1u : tail == 4 ? ((d.fast & 16) ? 1u : 0u) : 32u;
+        y |= need | (r << 5) | (tail == 3 ? 1u << 11 : 0u) | (tail == 4 ? 1u << 12 : 0u) |
+             ((uint32_t)(d.bkind & 3) << 13) | (1u << 15);
+    }
+    return make_uint2(x, y);
+}
+
 template <int NT, int L>
 struct TileSmem {
     static constexpr int T = NT * L;
@@ -265,8 +295,8 @@ struct TileSmem {
     static constexpr int NE = T + T / L + 1;
     uint4 w4[WPAD / 4];
     uint16_t E[NE];                 // exact path: exit past each position's segment (relative); then the start list
-    uint32_t flt[257];              // per opcode: word counts a start may have (low 16 bits min, high max)
-    uint2 fd[257];                  // per opcode: fast operand form (id mask, flags, form; fixed words, capability)
+    uint32_t fwc[257];              // per opcode: word counts a start may have, as min | (max - min + 1) << 16
+    uint2 vd[257];                  // per opcode: what validating a row needs (vdesc)
     uint8_t bnp[4][16];             // per bit-enum kind and mask: literal parameters of its known bits
     uint32_t far[T / 32];           // successor marks two or more segments ahead
     uint32_t sl_hi[NW];             // each warp's last segment's marks for the next warp's first segment
@@ -292,6 +322,61 @@ struct TileSmem {
     unsigned int vnext;                             // next row chunk to validate
 };
 
+// The full operand walk of row r starting at tile position p: forms with
+// strings, value enums and their parameters; rows that validation counts or
+// measures (capabilities, memory model, entry points, functions, integer and
+// float widths); rows longer than 32 words. Returns the row's required
+// capabilities and whether it inserted a result id into a bitmap. (Inlined:
+// an out-of-line call measured slower, with more instruction-fetch stalls.)
+struct SlowOut { uint32_t lo, hi, ins; };
+template <int NT, int L>
+__device__ __forceinline__ SlowOut slow_row(TileSmem<NT, L> &s, const uint32_t *src, uint32_t p, unsigned r,
+                                         uint32_t bound, uint32_t *arena, long long arena_off, uint32_t id_slots)
+{
+    constexpr int TH = TileSmem<NT, L>::TH;
+    const uint32_t *ws = reinterpret_cast<const uint32_t *>(s.w4);
+    SlowOut o{0u, 0u, 0u};
+    const uint32_t w0 = ws[pwu<L>(p)];
+    const uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
+    const spvt::OpDesc &d = g_spv_tables.ops[op];          // a known opcode (< 256)
+    auto iw = [&](uint32_t q) -> uint32_t {
+        const uint32_t a = p + q;
+        return a < (uint32_t)TH ? ws[pwu<L>(a)] : __ldg(src + a);
+    };
+    uint32_t ri = 0;
+    if (d.flags & 4) {
+        const uint32_t q = (d.flags & 2) ? 2u : 1u;
+        if (q < wc) ri = iw(q);
+    }
+    if (d.flags & 8) {            // the few opcodes validation counts or measures
+        if (op == 17) {
+            atomicAdd(&s.n_cap, 1u);
+            if (wc >= 2) { const uint32_t c = iw(1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); }
+        }
+        else if (op == 14) atomicAdd(&s.n_mm, 1u);
+        else if (op == 15) atomicAdd(&s.n_ep, 1u);
+        else if (op == 54) atomicAdd(&s.n_fn, 1u);
+    }
+    const Walk wk = walk_instruction(iw, wc, d, bound);
+    if (!wk.ok) atomicMin(&s.err_key, make_key(r, R_BADOP, 0));
+    else if (wk.oob) atomicMin(&s.err_key, make_key(r, R_OOB, 0));
+    else {
+        if ((d.flags & 4) && arena_off >= 0) {
+            if (id_slots == 0) {
+                atomicOr(&arena[arena_off + (ri >> 5)], 1u << (ri & 31));
+                o.ins = 1;
+            } else if (idset_insert(arena + arena_off, id_slots, ri)) {
+                atomicOr(&s.flags, MF_DUP);
+            }
+        }
+        uint64_t req = wk.req;
+        if (d.flags & 8) req |= width_caps(iw, op, wc);
+        o.lo = (uint32_t)req;
+        o.hi = (uint32_t)(req >> 32);
+    }
+    return o;
+}
+
 template <int NT, int L>
 __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
 {
@@ -313,7 +398,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
 
     // per-opcode tables, once per CTA
     for (int o = tid; o < 257; o += NT) {
-        uint32_t f = 0xffffu;                      // min 0xffff, max 0: no word count fits
+        uint32_t f = 0u;                           // no word count fits
         if (o < 256) {
             const spvt::OpDesc &d = TB.ops[o];
             if (d.flags & 1) {
@@ -326,14 +411,13 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
                 } else {
                     mn = 1u + ((d.flags >> 1) & 1u) + ((d.flags >> 2) & 1u);
                 }
-                f = mn | (mx << 16);
+                f = mn | ((mx - mn + 1u) << 16);
             }
-            s.fd[o] = make_uint2((uint32_t)d.id_mask | ((uint32_t)d.flags << 16) | ((uint32_t)d.fast << 24),
-                                 (uint32_t)d.nfixed | ((uint32_t)(uint8_t)d.cap << 8) | ((uint32_t)d.bkind << 16));
+            s.vd[o] = vdesc(d);
         } else {
-            s.fd[o] = make_uint2(0u, 0u);          // opcodes past the table: unknown
+            s.vd[o] = make_uint2(0u, 0u);          // opcodes past the table: unknown
         }
-        s.flt[o] = f;
+        s.fwc[o] = f;
     }
     // a bit-enum word's parameters: its known bits all lie below bit 4
     static_assert(spvt::NUM_BKINDS == 4, "bit-enum kinds");
@@ -408,57 +492,87 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
         //    my segment's words also go straight to the encoded output
         uint32_t X = 0, sl = 0, ne = 0;
         const int n_copy = (int)(end_s < (uint32_t)T ? end_s : (uint32_t)T);   // tile-local end of the module's words
-        if (live || (P.out && P.out_vec)) {
-            uint32_t wv[L];
+        if (P.out && P.out_vec) {
+            // 5. encode: in the fused path every field an instruction writes back
+            // (first word from wc/op, result type, result id) is decoded from the
+            // staged words themselves, so the re-encoded tile is the staged tile;
+            // the header bound is patched by the finalize pass
+            uint32_t *dst = P.out + tbase;
             #pragma unroll
             for (int c = 0; c < L / 4; c++) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(ws + pw<L>(lo + 4 * c));
-                wv[4 * c] = v.x; wv[4 * c + 1] = v.y; wv[4 * c + 2] = v.z; wv[4 * c + 3] = v.w;
-            }
-            if (P.out && P.out_vec) {
-                // 5. encode: in the fused path every field an instruction writes back
-                // (first word from wc/op, result type, result id) is decoded from the
-                // staged words themselves, so the re-encoded tile is the staged tile;
-                // the header bound is patched by the finalize pass
-                uint32_t *dst = P.out + tbase;
-                #pragma unroll
-                for (int c = 0; c < L / 4; c++) {
-                    const int s0 = lo + 4 * c;
-                    if (s0 >= lo_ok && s0 + 4 <= n_copy) {
-                        *reinterpret_cast<uint4 *>(dst + s0) = make_uint4(wv[4 * c], wv[4 * c + 1], wv[4 * c + 2], wv[4 * c + 3]);
-                    } else if (s0 < n_copy && s0 + 4 > lo_ok) {
-                        #pragma unroll
-                        for (int q = 0; q < 4; q++)
-                            if (s0 + q >= lo_ok && s0 + q < n_copy) dst[s0 + q] = wv[4 * c + q];
-                    }
+                const int s0 = lo + 4 * c;
+                const uint4 v = *reinterpret_cast<const uint4 *>(ws + pw<L>(s0));
+                if (s0 >= lo_ok && s0 + 4 <= n_copy) {
+                    *reinterpret_cast<uint4 *>(dst + s0) = v;
+                } else if (s0 < n_copy && s0 + 4 > lo_ok) {
+                    const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+                    #pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        if (s0 + q >= lo_ok && s0 + q < n_copy) dst[s0 + q] = vv[q];
                 }
             }
+        }
+        {
             if (live) {
-                if (k == 0 && tid == 0) {              // the module header is never a start
+                if (k == 0 && tid == 0) {
+                    // the module header is never a start: its staged words are
+                    // cleared while this thread guesses (only it reads them here)
+                    // and put back afterwards
                     #pragma unroll
                     for (int j = 0; j < 8; j++)
-                        if (j < (int)ph + 5) wv[j] = 0u;
+                        if (j < (int)ph + 5) ws[pw<L>(j)] = 0u;
                 }
                 const int lim = (int)tile_n - lo;      // a successor at or past lim leaves the tile
-                uint32_t ex = 0, farm = 0;
+                // a word w is a candidate when, with its opcode's entry f = min |
+                // (max - min + 1) << 16, w - (min << 16) < (max - min + 1) << 16: the
+                // word count lies in [min, max] (the opcode bits stay below bit 16,
+                // and a count below min wraps to a value no smaller than the
+                // bound). Successors in this or the next segment are marked
+                // here; farther ones (long instructions, or leaving the tile) are
+                // listed in `big` and settled after the loop.
+                constexpr uint32_t SLM = 2 * L >= 32 ? FULL : (1u << (2 * L)) - 1u;
+                uint32_t ex = 0, big = 0;
                 #pragma unroll
-                for (int j = 0; j < L; j++) {
-                    const uint32_t w = wv[j], wc = w >> 16, op = w & 0xffffu;
-                    const uint32_t f = s.flt[op < 256u ? op : 256u];
-                    const bool pl = wc >= (f & 0xffffu) && wc <= (f >> 16);
-                    const int nx = j + (int)wc;
-                    X |= pl ? (1u << j) : 0u;
-                    const bool leaves = pl && nx >= lim;
-                    ne += leaves ? 1u : 0u;
-                    ex = leaves ? (uint32_t)(lo + nx) : ex;
-                    sl |= (pl && nx < lim && nx < 2 * L) ? (1u << (nx & 31)) : 0u;
-                    farm |= (pl && nx < lim && nx >= 2 * L) ? (1u << j) : 0u;
+                for (int c = 0; c < L / 4; c++) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(ws + pw<L>(lo + 4 * c));
+                    const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+                    #pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const int j = 4 * c + q;
+                        const uint32_t w = vv[q], op = w & 0xffffu;
+                        const uint32_t f = s.fwc[op < 256u ? op : 256u];
+                        const uint32_t nx = (uint32_t)j + (w >> 16);
+                        if (w - (f << 16) < (f & 0xffff0000u)) {
+                            X |= 1u << j;
+                            sl |= shl_clamp(1u, nx) & SLM;
+                            if (nx >= 2u * L) big |= 1u << j;
+                        }
+                    }
                 }
-                while (farm) {                         // successors two or more segments ahead (long instructions)
-                    const int j = __ffs(farm) - 1;
-                    farm &= farm - 1;
-                    const int at = lo + j + (int)(ws[pw<L>(lo + j)] >> 16);
+                if (lim < 2 * L) {
+                    // the tile ends inside this segment or the next: successors
+                    // at or past lim leave the tile instead of being marked
+                    sl = 0; big = 0;
+                    for (uint32_t x = X; x; x &= x - 1) {
+                        const int j = __ffs(x) - 1;
+                        const int nx = j + (int)(ws[pw<L>(lo + j)] >> 16);
+                        if (nx >= lim) { ne++; ex = (uint32_t)(lo + nx); }
+                        else if (nx < 2 * L) sl |= 1u << nx;
+                        else big |= 1u << j;
+                    }
+                }
+                while (big) {                          // successors two or more segments ahead
+                    const int j = __ffs(big) - 1;
+                    big &= big - 1;
+                    const int nx = j + (int)(ws[pw<L>(lo + j)] >> 16);
+                    if (nx >= lim) { ne++; ex = (uint32_t)(lo + nx); continue; }
+                    const int at = lo + nx;
                     atomicOr(&s.far[at >> 5], 1u << (at & 31));
+                }
+                if (k == 0 && tid == 0) {
+                    #pragma unroll
+                    for (int j = 0; j < 8; j++)
+                        if (j >= (int)ph && j < (int)ph + 5) ws[pw<L>(j)] = __ldg(src + j);
                 }
                 s.X[tid] = (uint16_t)X;
                 if (lane == 31) s.sl_hi[wid] = sl;
@@ -874,59 +988,16 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
         const long long arena_off = P.ms[m].arena_off;
         const uint32_t id_slots = P.ms[m].id_slots;
         uint32_t acc_lo = 0, acc_hi = 0, acc_ins = 0;  // this lane's requirements and insertions
-        // the full operand walk of row r (forms with strings, value enums and
-        // their parameters; rows that validation counts or measures; rows
-        // reaching past the tile or longer than 32 words)
-        auto full_walk = [&](unsigned r) {
-            const uint32_t p = S16[r];
-            const uint32_t w0 = ws[pwu<L>(p)];
-            const uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
-            const spvt::OpDesc &d = TB.ops[op];          // a known opcode (< 256)
-            auto iw = [&](uint32_t q) -> uint32_t {
-                const uint32_t a = p + q;
-                return a < (uint32_t)TH ? ws[pwu<L>(a)] : __ldg(src + a);
-            };
-            auto sw = [&](uint32_t q) -> uint32_t { return ws[pwu<L>(p + q)]; };
-            uint32_t ri = 0;
-            if (d.flags & 4) {
-                const uint32_t q = (d.flags & 2) ? 2u : 1u;
-                if (q < wc) ri = sw(q);
-            }
-            if (d.flags & 8) {            // the few opcodes validation counts or measures
-                if (op == 17) { atomicAdd(&s.n_cap, 1u); if (wc >= 2) { uint32_t c = iw(1); if (c < 32) atomicOr(&s.decl_lo, 1u << c); else if (c < 64) atomicOr(&s.decl_hi, 1u << (c - 32)); } }
-                else if (op == 14) atomicAdd(&s.n_mm, 1u);
-                else if (op == 15) atomicAdd(&s.n_ep, 1u);
-                else if (op == 54) atomicAdd(&s.n_fn, 1u);
-            }
-            // an instruction wholly inside the staged words (almost every one)
-            // reads them without the per-word range check
-            const Walk wk = p + wc <= (uint32_t)TH ? walk_instruction(sw, wc, d, bound)
-                                                   : walk_instruction(iw, wc, d, bound);
-            if (!wk.ok) atomicMin(&s.err_key, make_key(r, R_BADOP, 0));
-            else if (wk.oob) atomicMin(&s.err_key, make_key(r, R_OOB, 0));
-            else {
-                if ((d.flags & 4) && arena_off >= 0) {
-                    if (id_slots == 0) {
-                        atomicOr(&P.arena[arena_off + (ri >> 5)], 1u << (ri & 31));
-                        acc_ins++;
-                    } else if (idset_insert(P.arena + arena_off, id_slots, ri)) {
-                        atomicOr(&s.flags, MF_DUP);
-                    }
-                }
-                uint64_t req = wk.req;
-                if (d.flags & 8) req |= width_caps(iw, op, wc);
-                acc_lo |= (uint32_t)req;
-                acc_hi |= (uint32_t)(req >> 32);
-            }
-        };
         if (P.validate) {
-            // rows in chunks of 32 from a shared counter. A row in the fast operand form (fixed ids
-            // and literals, then a plain tail or one bit-enum word; wholly in
-            // the tile, at most 32 words) is checked here, in the order of
-            // section 3.4.5's checks: known opcode, its word count against the
-            // form, every id operand in [1, bound); then its result id goes
-            // into the module's id set and the opcode's capability into the
-            // tile's requirements. Any other row takes the full operand walk.
+            // rows in chunks of 32 from a shared counter. A row in the fast
+            // operand form (fixed ids and literals, then a plain tail or one
+            // bit-enum word; at most 32 words, all staged: p < T and the halo
+            // holds 64 more) is checked here, in the order of section 3.4.5's
+            // checks: known opcode, its word count against the form, every id
+            // operand in [1, bound); then its result id goes into the module's
+            // id set and the opcode's capability into the tile's requirements.
+            // Any other row takes the full operand walk (slow_row).
+            static_assert(HALO >= 32, "fast rows read up to 32 staged words");
             for (;;) {
                 unsigned rb = 0;
                 if (lane == 0) rb = atomicAdd(&s.vnext, 32u);
@@ -935,36 +1006,41 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
                 const unsigned r = rb + (unsigned)lane;
                 const bool have = r < tile_count;
                 const uint32_t p = have ? (uint32_t)S16[r] : 0u;
-                const uint32_t w0 = ws[pwu<L>(p)];
+                const uint32_t a0 = pwu<L>(p);
+                // words 1..8 of the row lie at a0 + i, or 4 further once past
+                // the segment's end (position `cross`): one boundary at most
+                const uint32_t cross = (uint32_t)L - p % (uint32_t)L;
+                const uint32_t w0 = ws[a0];
                 const uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
-                const uint2 fdv = s.fd[op < 256u ? op : 256u];
-                const uint32_t flags = (fdv.x >> 16) & 0xffu, form = fdv.x >> 24;
-                const uint32_t need = 1u + (fdv.y & 0xffu), tail = (form >> 1) & 7u;
-                const bool known = have && (flags & 1u);
-                const bool fastrow = known && (form & 1u) && !(flags & 8u) && p + wc <= (uint32_t)T && wc <= 32u;
-                // a bit-enum tail's word, staged: p < T and need <= 16
-                const uint32_t np = s.bnp[(fdv.y >> 16) & 3u][ws[pwu<L>(p + need)] & 15u];
-                bool ok;
-                if (tail == 0) ok = wc == need;
-                else if (tail == 4) ok = wc == need ? (form & 16u) != 0 : wc == need + 1u + np;
-                else ok = wc >= need && (tail != 3 || ((wc - need) & 1u) == 0);
+                const uint2 vd = s.vd[op < 256u ? op : 256u];
+                const bool known = have && ((vd.y >> 16) & 1u);
+                const bool fastrow = have && ((vd.y >> 15) & 1u) && wc <= 32u;
+                const uint32_t need = vd.y & 31u;
+                const uint32_t dw = wc - need;                    // words past the fixed operands
+                const uint32_t np = s.bnp[(vd.y >> 13) & 3u][ws[pwu<L>(p + need)] & 15u];
+                bool ok = (dw < ((vd.y >> 5) & 63u) && !(dw & (vd.y >> 11) & 1u)) ||
+                          (((vd.y >> 12) & 1u) && dw == 1u + np);
                 ok = ok && fastrow;
-                uint32_t idm = ok ? (fdv.x & 0xffffu) : 0u;
-                if (ok && (tail == 1 || tail == 3))
-                    idm |= (wc == 32u ? FULL : ((1u << wc) - 1u)) & ~((1u << need) - 1u);
-                bool oob = false;
-                while (idm) {
-                    const uint32_t i = (uint32_t)(__ffs(idm) - 1);
-                    idm &= idm - 1;
-                    oob |= ws[pwu<L>(p + i)] - 1u >= bound - 1u;
+                const uint32_t idm = ok ? vd.x & (shl_clamp(2u, wc - 1u) - 1u) : 0u;
+                uint32_t mx = 0, ri = 0;                          // largest id - 1; the result id
+                const uint32_t qi = 1u + ((vd.y >> 18) & 1u);     // the result id's word
+                #pragma unroll
+                for (int i = 1; i <= 8; i++) {
+                    const uint32_t v = ws[a0 + (uint32_t)i + ((uint32_t)i >= cross ? 4u : 0u)];
+                    if ((idm >> i) & 1u) mx = max(mx, v - 1u);
+                    if (i <= 2 && (uint32_t)i == qi) ri = v;
                 }
-                if ((have && !known) || (fastrow && !ok) || oob)
+                if (idm >> 9) {                                   // ids past word 8 (long id tails)
+                    for (uint32_t x = idm >> 9 << 9; x; x &= x - 1)
+                        mx = max(mx, ws[pwu<L>(p + (uint32_t)(__ffs(x) - 1))] - 1u);
+                }
+                const bool oob = idm != 0 && mx >= bound - 1u;
+                if (have && (!known || (fastrow && !ok) || oob))
                     atomicMin(&s.err_key, make_key(r, !known ? R_UNKNOWN : (!ok ? R_BADOP : R_OOB), 0));
                 const bool good = ok && !oob;
-                const int cap = (int)(int8_t)((fdv.y >> 8) & 0xffu);
-                if (good && cap >= 0) { if (cap < 32) acc_lo |= 1u << cap; else acc_hi |= 1u << (cap - 32); }
-                if (good && (flags & 4u) && arena_off >= 0) {
-                    const uint32_t ri = ws[pwu<L>(p + ((flags & 2u) ? 2u : 1u))];
+                const uint32_t cap = vd.y >> 24;                  // 0xff: none
+                if (good && cap < 64u) { if (cap & 32u) acc_hi |= 1u << (cap & 31u); else acc_lo |= 1u << cap; }
+                if (good && ((vd.y >> 17) & 1u) && arena_off >= 0) {
                     if (id_slots == 0) {
                         // no wait on the old value: duplicates show up later as
                         // fewer bits set than ids inserted
@@ -974,9 +1050,11 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
                         atomicOr(&s.flags, MF_DUP);
                     }
                 }
-                // the rest take the full operand walk, in the same chunk
                 const bool slow = known && !fastrow;
-                if (__any_sync(FULL, slow) && slow) full_walk(r);
+                if (__any_sync(FULL, slow) && slow) {
+                    const SlowOut so = slow_row<NT, L>(s, src, p, r, bound, P.arena, arena_off, id_slots);
+                    acc_lo |= so.lo; acc_hi |= so.hi; acc_ins += so.ins;
+                }
             }
             // this warp's requirements and insertions, once for all its chunks
             const uint32_t rlo = __reduce_or_sync(FULL, acc_lo);
@@ -1021,7 +1099,8 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
                     const uint32_t p = S16[r];
                     const uint32_t w0 = ws[pwu<L>(p)];
                     const uint32_t op = w0 & 0xffffu, wc = w0 >> 16;
-                    const uint32_t flags = (s.fd[op < 256u ? op : 256u].x >> 16) & 0xffu;
+                    const uint32_t vy = s.vd[op < 256u ? op : 256u].y;
+                    const uint32_t flags = ((vy >> 17) & 1u ? 4u : 0u) | ((vy >> 18) & 1u ? 2u : 0u);
                     const uint32_t w1 = ws[pwu<L>(p + 1)], w2 = ws[pwu<L>(p + 2)];
                     uint32_t rt = 0, ri = 0;
                     if (flags & 2u) { if (wc > 1) rt = w1; if ((flags & 4u) && wc > 2) ri = w2; }

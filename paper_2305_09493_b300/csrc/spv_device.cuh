@@ -141,6 +141,14 @@ __device__ __forceinline__ void st_relaxed32(uint32_t *p, uint32_t v)
 }
 __device__ __forceinline__ void spin_pause() { __nanosleep(32); }
 
+// x << n with the shift clamped at 32 (PTX shl): 0 for n >= 32
+__device__ __forceinline__ uint32_t shl_clamp(uint32_t x, uint32_t n)
+{
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(n));
+    return r;
+}
+
 // Decoupled look-back by one warp (all 32 lanes) over state[0 .. hi]: a state
 // is 0 (not yet published), inclusive (flag `incl`: the sum of every state up
 // to and including its own) or an aggregate (any other flag: its own count);
