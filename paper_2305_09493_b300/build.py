@@ -36,7 +36,9 @@ def _headers() -> list:
 
 def _source_hash(src: str, extra) -> str:
     h = hashlib.sha256()
-    h.update(" ".join(ARCH + FLAGS + list(extra)).encode())
+    # the flags as written here, the include path relative to the repository
+    # (a copy of the tree elsewhere keeps its hashes)
+    h.update(" ".join(ARCH + FLAGS + list(extra)).replace(ROOT, "<root>").encode())
     h.update(_read(os.path.join(CSRC, src)))
     for hp in _headers():
         h.update(os.path.basename(hp).encode())
