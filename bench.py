@@ -148,8 +148,17 @@ class Clocks:
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         time.sleep(0.25)
+        # bounded: an nvidia-smi blocked inside the driver must not hold the
+        # bench (terminate, then kill, then go on with the samples written)
         self.p.terminate()
-        self.p.wait()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                pass
         self.f.seek(0)
         rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
         os.unlink(self.f.name)

@@ -562,9 +562,10 @@ extern "C" int spv_serve_replay(spv_server *s, int32_t n, const uint32_t *const 
     std::atomic<int32_t> submitted{0};
     std::atomic<int> failed{0};
     std::atomic<int64_t> busy{0};
+    std::atomic<bool> stop{false};                   // the collector gave up: submit no more
     const uint64_t t0 = now_ns() + 1000000;         // start 1 ms from now
     std::thread sub([&] {
-        for (int32_t i = 0; i < n; i++) {
+        for (int32_t i = 0; i < n && !stop.load(std::memory_order_relaxed); i++) {
             const uint64_t target = t0 + (uint64_t)arrive_ns[i];
             for (;;) {
                 const uint64_t now = now_ns();
@@ -575,6 +576,7 @@ extern "C" int spv_serve_replay(spv_server *s, int32_t n, const uint32_t *const 
                 const int rc = spv_serve_submit(s, mods[i], n_words[i], &tickets[(size_t)i]);
                 if (rc == SPV_SUCCESS) break;
                 if (rc != SPV_E_BUSY) { failed.store(rc); submitted.store(n + 1, std::memory_order_release); return; }
+                if (stop.load(std::memory_order_relaxed)) return;
                 busy.fetch_add(1);
                 std::this_thread::sleep_for(std::chrono::microseconds(10));
             }
@@ -594,6 +596,7 @@ extern "C" int spv_serve_replay(spv_server *s, int32_t n, const uint32_t *const 
         if (batch_modules) batch_modules[i] = r.batch_modules;
         spv_serve_release(s, tickets[(size_t)i]);
     }
+    if (rc != SPV_SUCCESS) stop.store(true, std::memory_order_relaxed);
     sub.join();
     if (busy_retries) *busy_retries = busy.load();
     return rc;
