@@ -987,7 +987,6 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
             const long long tt = (long long)__shfl_sync(0xffffffffu, ticket, 0);
             if (lane == 0) {
                 s.tile = tt;
-                s.gave_up = 0;
                 s.fnext = 0;
                 s.mnext = 0;
                 s.wlo = ~0ull;
@@ -1022,6 +1021,10 @@ __global__ void __launch_bounds__(DNT, SPV_DIS_MIN_BLOCKS) k_dis_main(DP P)
         if (wid == 0 && !prefetched) setup_tile();
         prefetched = false;
         if (tid < NSHAPE) s.cls_n[tid] = 0;
+        // the look-back's timeout flag is cleared here, where every thread has
+        // read the last tile's (warp 0 sets up the next tile while the others
+        // may still be reading it)
+        if (tid == 0) s.gave_up = 0;
         __syncthreads();
         const long long t = s.tile;
         if (t >= ntiles) break;
