@@ -499,7 +499,7 @@ int spv_serve_poll(spv_server *s, uint64_t ticket, spv_result *out);
 int spv_serve_wait(spv_server *s, uint64_t ticket, spv_result *out, int64_t timeout_us);
 /* Release a done module's results and its share of the device pool. */
 int spv_serve_release(spv_server *s, uint64_t ticket);
-/* Stop the scheduler, wait for in-flight batches, free everything. */
+/* Stop the scheduler, wait for in-flight batches, free everything (modules still queued are dropped). */
 void spv_serve_destroy(spv_server *s);
 /*
  * Load replay, for measuring the server under an arrival process: module i

@@ -163,11 +163,17 @@ struct spv_server {
 
 namespace {
 
+// the stream callback of a batch. The server is read before the batch is
+// signaled: from then on the scheduler may complete the batch and its
+// results may be released, freeing it while this callback still runs (a read
+// of the freed batch here once blocked the driver's callback thread, and
+// with it every stream of the server).
 void CUDART_CB on_stage(void *p)
 {
     Batch *b = (Batch *)p;
+    spv_server *srv = b->srv;
     b->signaled.fetch_add(1);
-    b->srv->cv.notify_all();
+    srv->cv.notify_all();
 }
 
 bool dalloc(spv_server *s, Region &r, size_t bytes)
@@ -211,42 +217,50 @@ void finish_requests(spv_server *s, Batch *b)
 
 // launch a batch on a free slot; returns false when memory is short. The
 // server lock is held for the bookkeeping and released for the CUDA calls.
+// The batch is the waiting modules from the front of the queue, up to the
+// batch limits; when its memory does not fit (the pools are first-fit and
+// fragment over a long run), it takes half as many, down to the oldest
+// module alone. A batch that only grew while its memory did not fit would
+// never go out: the queue keeps growing behind it.
 bool launch(spv_server *s, int slot, std::unique_lock<std::mutex> &lk)
 {
-    std::vector<Req *> take;
+    size_t cnt = 0;
     int64_t words = 0;
-    int maxm = s->cfg.max_batch_modules;
-    while (!s->queue.empty() && (int)take.size() < maxm) {
-        Req *r = s->queue.front();
-        if (!take.empty() && words + r->n_words > s->cfg.max_batch_words) break;
-        take.push_back(r);
+    for (Req *r : s->queue) {
+        if ((int)cnt >= s->cfg.max_batch_modules) break;
+        if (cnt && words + r->n_words > s->cfg.max_batch_words) break;
         words += r->n_words;
-        s->queue.pop_front();
+        cnt++;
     }
-    if (take.empty()) return false;
+    if (!cnt) return false;
     Batch *b = new Batch();
+    for (;;) {
+        const int n = (int)cnt;
+        b->ws_bytes = spv_workspace_bytes(n, words, 0, nullptr);
+        b->dws_bytes = spv_dis_workspace_bytes(n, words, words, 0);
+        b->text_cap = 12ull * (uint64_t)words + 512ull * n + 1024;
+        size_t tmp_bytes = up(b->ws_bytes) + up(b->dws_bytes) + up(b->text_cap) + up(4 * (size_t)n) +
+                           up(8 * (size_t)n) + up(8 * (size_t)(n + 1)) + up(4 * (size_t)n) + 4096;
+        size_t small = up(8 * (size_t)(n + 1)) * 3 + up(4 * (size_t)n) * 2 + up(8 * (size_t)n) + 4096;
+        bool ok = dalloc(s, b->dev, persistent_bytes(n, words));
+        ok = ok && dalloc(s, b->tmp, tmp_bytes);
+        ok = ok && halloc(s, b->pin_small, small);
+        ok = ok && halloc(s, b->pin_text, b->text_cap + 1);
+        if (ok) break;
+        dfree(s, b->dev); dfree(s, b->tmp); hfree(s, b->pin_small); hfree(s, b->pin_text);
+        if (cnt == 1) { delete b; return false; }
+        cnt = (cnt + 1) / 2;
+        words = 0;
+        for (size_t i = 0; i < cnt; i++) words += s->queue[i]->n_words;
+    }
+    std::vector<Req *> take(s->queue.begin(), s->queue.begin() + (long)cnt);
+    s->queue.erase(s->queue.begin(), s->queue.begin() + (long)cnt);
     b->srv = s;
     b->reqs = take;
     b->words = words;
-    b->n = (int)take.size();
+    b->n = (int)cnt;
     b->slot = slot;
     int n = b->n;
-    b->ws_bytes = spv_workspace_bytes(n, words, 0, nullptr);
-    b->dws_bytes = spv_dis_workspace_bytes(n, words, words, 0);
-    b->text_cap = 12ull * (uint64_t)words + 512ull * n + 1024;
-    size_t tmp_bytes = up(b->ws_bytes) + up(b->dws_bytes) + up(b->text_cap) + up(4 * (size_t)n) +
-                       up(8 * (size_t)n) + up(8 * (size_t)(n + 1)) + up(4 * (size_t)n) + 4096;
-    size_t small = up(8 * (size_t)(n + 1)) * 3 + up(4 * (size_t)n) * 2 + up(8 * (size_t)n) + 4096;
-    bool ok = dalloc(s, b->dev, persistent_bytes(n, words));
-    ok = ok && dalloc(s, b->tmp, tmp_bytes);
-    ok = ok && halloc(s, b->pin_small, small);
-    ok = ok && halloc(s, b->pin_text, b->text_cap + 1);
-    if (!ok) {
-        dfree(s, b->dev); dfree(s, b->tmp); hfree(s, b->pin_small); hfree(s, b->pin_text);
-        for (auto it = take.rbegin(); it != take.rend(); ++it) s->queue.push_front(*it);
-        delete b;
-        return false;
-    }
     Carver dv{s->dpool + b->dev.off};
     b->d_words = dv.take<uint32_t>(words);
     b->d_off = dv.take<int64_t>(n + 1);
@@ -388,9 +402,10 @@ void scheduler(spv_server *s)
             }
             k++;
         }
-        if (s->stop && s->queue.empty() && s->inflight.empty()) break;
+        // stopping: the batches in flight finish, queued modules are dropped
+        if (s->stop && s->inflight.empty()) break;
         bool launched = false;
-        for (int slot = 0; slot < NSLOT && !s->queue.empty(); slot++)
+        for (int slot = 0; slot < NSLOT && !s->stop && !s->queue.empty(); slot++)
             if (!s->slot_busy[slot]) launched |= launch(s, slot, lk);
         if (!launched) s->cv.wait_for(lk, std::chrono::microseconds(50));
     }
