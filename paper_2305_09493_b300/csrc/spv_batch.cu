@@ -593,8 +593,9 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
                 uint32_t r2 = ne | ((uint32_t)__popc(X) << 16);
                 r1 = __reduce_add_sync(FULL, r1);
                 r2 = __reduce_add_sync(FULL, r2);
-                if (lane == 0) { atomicAdd(&s.cnt1, r1); atomicAdd(&s.cnt2, r2); }
-                if (X) atomicMin(&s.xfirst, (uint32_t)(lo + __ffs(X) - 1));
+                // the first guessed start: a minimum per warp, then one shared atomic per warp
+                const uint32_t xf = __reduce_min_sync(FULL, X ? (uint32_t)(lo + __ffs(X) - 1) : DEAD);
+                if (lane == 0) { atomicAdd(&s.cnt1, r1); atomicAdd(&s.cnt2, r2); if (xf != DEAD) atomicMin(&s.xfirst, xf); }
             }
             __syncthreads();
         };
