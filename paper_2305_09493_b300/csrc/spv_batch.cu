@@ -314,7 +314,6 @@ struct TileSmem {
     int need_exact;
     int count_pub;                  // the row count is published already
     unsigned long long row_base;
-    unsigned int count;
     int timeout;
     // aggregates flushed once per tile
     unsigned long long err_key;
@@ -960,21 +959,17 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
         for (int d = 1; d < 32; d <<= 1) { unsigned v = __shfl_up_sync(FULL, incl, d); if (lane >= d) incl += v; }
         if (lane == 31) s.warp_tot[wid] = incl;
         __syncthreads();
+        // every warp scans the warp counts itself (no barrier after a scan by
+        // one warp); warp 0 publishes the tile's count
         const bool stalled = (g == P.stall_tile || g == P.stall_map_tile);
-        if (wid == 0) {                          // block scan of the warp counts; publish the tile's count
-            unsigned v = lane < NW ? s.warp_tot[lane] : 0;
-            #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) { unsigned u = __shfl_up_sync(FULL, v, d); if (lane >= d) v += u; }
-            if (lane < NW) s.warp_tot[lane] = v;
-            unsigned total = __shfl_sync(FULL, v, NW - 1);
-            if (lane == 0) {
-                s.count = total;
-                if (!stalled && !s.count_pub) st_relaxed(&P.cstate[g], (g == 0 ? F_EXIT : F_MAP) | total);
-            }
-        }
-        __syncthreads();
-        const unsigned tile_count = s.count;
-        const unsigned my_off = (wid ? s.warp_tot[wid - 1] : 0) + incl - cnt;
+        unsigned wv = lane < NW ? s.warp_tot[lane] : 0;
+        #pragma unroll
+        for (int d = 1; d < NW; d <<= 1) { unsigned u = __shfl_up_sync(FULL, wv, d); if (lane >= d) wv += u; }
+        const unsigned tile_count = __shfl_sync(FULL, wv, NW - 1);
+        const unsigned wpre = __shfl_sync(FULL, wv, wid > 0 ? wid - 1 : 0);
+        if (wid == 0 && lane == 0 && !stalled && !s.count_pub)
+            st_relaxed(&P.cstate[g], (g == 0 ? F_EXIT : F_MAP) | tile_count);
+        const unsigned my_off = (wid ? wpre : 0u) + incl - cnt;
         // error keys hold tile-local rows until the flush adds the tile's first row
         if (ferr >= 0 && live) atomicMin(&s.err_key, make_key(my_off + cnt, R_FRAME, (uint32_t)ferr));
         // start list (reuses E)
