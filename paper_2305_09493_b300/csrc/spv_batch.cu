@@ -721,6 +721,25 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
         };
         if (live && !fast) exact_maps();
 
+        // A tile whose entry every thread knows (its first guessed start, or
+        // word 5 of a module's first tile on the guessed chain) has published
+        // its exit and row count above: it skips warp 0's section and the
+        // barrier after it.
+        bool quick = false;
+        {
+            const uint32_t e0 = ph + 5;
+            const bool first_on_chain = k == 0 && e0 < tile_n && ((s.X[e0 / L] >> (e0 % L)) & 1u);
+            const uint32_t nX = s.cnt2 >> 16;
+            quick = live && fast && nX > 0 && g != P.stall_tile && g != P.stall_map_tile && (spec_tile || first_on_chain);
+        }
+        const uint32_t qentry = quick ? (spec_tile ? s.xfirst : ph + 5) : DEAD;
+        if (quick) {
+            if (P.out && !P.out_vec) {
+                // encode word by word when the output buffer's 16-byte phase is not the words'
+                uint32_t *dst = P.out + tbase;
+                for (int i = tid + lo_ok; i < n_copy; i += NT) dst[i] = ws[pw<L>(i)];
+            }
+        } else {
         // 3. warp 0: the tile map for entries 0..31, published; the look-back
         //    for the tile's entry; the tile's exit, published. Meanwhile the
         //    other warps encode.
@@ -903,8 +922,9 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
             for (int i = tid - 32 + lo_ok; i < n_copy; i += NT - 32) dst[i] = ws[pw<L>(i)];
         }
         __syncthreads();
+        }
         // the entry missed the guessed chain: the exact path for this tile's starts
-        const bool need_exact = s.need_exact != 0;
+        const bool need_exact = !quick && s.need_exact != 0;
         if (need_exact) {
             exact_maps();
             if (tid == 0) {
@@ -921,7 +941,7 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_tile(Params P)
         uint32_t mask = 0;
         int ferr = -1;          // 0 zero word count, 1 truncated
         if (fast && !need_exact) {
-            const uint32_t e = s.entry;
+            const uint32_t e = quick ? qentry : s.entry;
             if (e != DEAD && e < tile_n) {
                 if (e <= (uint32_t)lo) mask = X;
                 else if (e < (uint32_t)(lo + L)) mask = X & ~((1u << (e - (uint32_t)lo)) - 1u);
